@@ -1,0 +1,437 @@
+"""Benchmark of the Wilson-Dirac hot path on GB300.
+
+A step is one full CG solve of D x = b on the normal equations to a true FP64
+residual of 1e-10 (section 2.2), on seeded synthetic inputs:
+
+  c2 (default)  16^4, Haar-random SU(3) links, kappa = 0.12, Gaussian source,
+                plain FP64 CG
+  c1            4^4, same recipe
+  c3            32^3 x 64, smoothed links exp(i 0.4 H), kappa = 0.124,
+                mixed precision (--inner f32|f16|f64, default f32)
+  c4            24^3 x 48, Haar links, kappa = 0.12, the 12 spin-colour point
+                sources solved together (multi-RHS CG, --inner f64|f32)
+
+value = GFLOP/s of the solve at 1320 flop per site per Dslash application
+(the Dslash flops of the 2 * iterations + 4 operator applications), i.e. the
+sustained Dslash rate inside the solver.  The roofline object describes the
+plain Dslash kernel of the solve's precision on the same lattice, timed alone.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FLOP_PER_SITE = 1320
+# Algorithmic bytes per site of one Dslash (each input field read once, output
+# written once): spinor in + links + spinor out.
+SPINOR_BYTES = {"f64": 192, "f32": 96, "f16": 52}
+LINK_BYTES = {("f64", 18): 576, ("f64", 12): 384, ("f32", 18): 288, ("f32", 12): 192, ("f16", 18): 144,
+              ("f16", 12): 96}
+PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
+WORKLOADS = {
+    "c1": dict(dims=(4, 4, 4, 4), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=1),
+    "c2": dict(dims=(16, 16, 16, 16), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=2),
+    "c3": dict(dims=(32, 32, 32, 64), links="smoothed", kappa=0.124, nrhs=1, inner="f32", seed=6),
+    "c4": dict(dims=(24, 24, 24, 48), links="haar", kappa=0.12, nrhs=12, inner="f64", seed=7),
+}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dslash_bytes(prec: str, recon: int) -> int:
+    return 2 * SPINOR_BYTES[prec] + LINK_BYTES[(prec, recon)]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# FP64 peak of a GB300 from the nominal figure (1.25 TFLOP/s dense FP64).
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1810_04201_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, n), "rb") as f:
+                h.update(n.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch recorded by ncu for this kernel, if the sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("csrc_hash") != csrc_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(w, rank):
+    from paper_1810_04201_gb300 import gen
+    seed = w["seed"] + 1000 * rank
+    dims = w["dims"]
+    if w["links"] == "haar":
+        U = gen.haar_links(dims, seed)
+    else:
+        U = gen.smoothed_links(dims, seed, eps=0.4)
+    if w["nrhs"] == 12:
+        b = gen.propagator_sources(dims)
+    else:
+        b = gen.gaussian_source(dims, seed)
+    return U, b
+
+
+def cpu_baseline(w, U, b, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the same solve (a fixed number
+    of CG iterations on the same lattice and source)."""
+    import oracle
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    b1 = b[0] if b.ndim == 4 else b
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.apply_D(U, b1, w["kappa"], dims)
+    t_apply = time.perf_counter() - t0
+    iters = max(1, min(200, int(budget_s / max(2 * t_apply, 1e-6)) - 2))
+    t0 = time.perf_counter()
+    _, info = oracle.cgnr(U, b1, w["kappa"], dims, tol=1e-10, max_iter=iters)
+    t = time.perf_counter() - t0
+    n_apply = 2 * info["iters"] + 5  # setup 2, per iteration 2, true residual 3
+    gflops = n_apply * FLOP_PER_SITE * V / t / 1e9
+    return {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"oracle CGNR on the same {'x'.join(map(str, dims))} lattice and source, "
+                      f"{info['iters']} iterations ({n_apply} operator applications) in {t:.1f} s, "
+                      f"{threads} OpenMP threads; 1320 flop/site per application"}
+
+
+def run_reference(args, w, rank, world):
+    """The reference arm: the CPU oracle, timed per step on a bounded sample."""
+    if rank != 0:
+        return
+    U, b = make_inputs(w, 0)
+    for _ in range(args.warmup):
+        cpu_baseline(w, U, b, budget_s=2.0)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, U, b, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / max(args.steps, 1), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, w),
+            "cpu_baseline": dict(last, value=round(v, 4)),
+            "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+METRIC = "Dslash GFLOP/s & HBM GB/s (% roofline); CG time-to-1e-10, mixed/multi-RHS vs FP64"
+
+
+def config_of(args, w):
+    return {"workload": f"{args.workload}: {'x'.join(map(str, w['dims']))} {w['links']} links, kappa={w['kappa']}, "
+                        f"{'12 point sources' if w['nrhs'] == 12 else 'Gaussian source'}, CGNR to true residual "
+                        f"1e-10, inner precision {args.inner or w['inner']}, recon {args.recon}",
+            "lattice": list(w["dims"]), "nrhs": w["nrhs"], "kappa": w["kappa"], "tol": 1e-10,
+            "inner_prec": args.inner or w["inner"], "recon": args.recon,
+            "l2": "flushed (512 MB write) before every timed step and every timed Dslash launch",
+            "parallelism": "replicas (one independent lattice per GPU)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wd", choices=["wd", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16"])
+    ap.add_argument("--recon", type=int, default=18, choices=[18, 12])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="also time the Dslash at 8^4, 12^4, 16^4, 24^4")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo" if args.impl == "reference" else "nccl")
+
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_1810_04201_gb300 import wd
+
+    inner = args.inner or w["inner"]
+    nrhs = w["nrhs"]
+    U, b = make_inputs(w, rank)
+    lat = wd.Lattice(w["dims"])
+    lat.set_gauge(U, recon=args.recon)
+    fb = lat.pack(b)
+    fx = lat.new_field(nrhs=nrhs)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    V = lat.V
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        fx.zero_()
+        res, st = lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=wd.PRECS[inner], nrhs=nrhs, raise_on_fail=False)
+        return res, st
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, launches, results = [], 0, None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results, st = solve()
+        e1.record(stream)
+        launches += lat.launches
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if st != 0:
+            raise RuntimeError(f"solve failed: {results}")
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = float(sum(times))
+    iters = max(r["iters"] for r in results)
+    n_apply = 2 * iters + 4 + 2 * max(r["reliable_updates"] for r in results)
+    flops_step = n_apply * FLOP_PER_SITE * V * nrhs
+
+    # ---- the Dslash kernel alone (same lattice, solve precision), CUDA events per launch
+    prec = inner if inner != "f64" or nrhs == 1 else "f64"
+    pid = PREC_ID[prec]
+    fin = lat.pack(b, pid)
+    fout = lat.new_field(pid, nrhs)
+    for _ in range(3):
+        lat.apply(w["kappa"], fin, fout, pid, nrhs)
+    dts = []
+    for _ in range(max(args.steps, 10)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.apply(w["kappa"], fin, fout, pid, nrhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dts.append(e0.elapsed_time(e1))
+        launches += 1
+    clk = clocks.stop()
+    d_ms = statistics.mean(dts)
+    d_gflops = FLOP_PER_SITE * V * nrhs / (d_ms * 1e-3) / 1e9
+    link_b = LINK_BYTES[(prec, args.recon)]
+    d_bytes = V * (nrhs * 2 * SPINOR_BYTES[prec] + link_b)
+    d_gbs = d_bytes / (d_ms * 1e-3) / 1e9
+    peaks = load_peaks()
+
+    # ---- end to end: canonical host buffers, copies inside the timed region
+    e2e = None
+    if nrhs == 1:
+        bt = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
+        xt = torch.zeros_like(bt).pin_memory()
+        lat.cg_canonical(w["kappa"], bt, xt, tol=1e-10, inner=wd.PRECS[inner])
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            xt.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, st = lat.cg_canonical(w["kappa"], bt, xt, tol=1e-10, inner=wd.PRECS[inner], raise_on_fail=False)
+            et.append(time.perf_counter() - t0)
+            launches_e2e = lat.launches
+        e2e_s = float(np.mean(et))
+        e2e = {"value": round(flops_step / e2e_s / 1e9, 3), "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(2 * bt.numel() * 16), "d2h_bytes_per_step": int(xt.numel() * 16),
+               "ms_per_step": round(e2e_s * 1e3, 3), "gpu_launches_per_step": int(launches_e2e)}
+
+    # max over ranks
+    step_ms = total_ms / args.steps
+    if dist:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * flops_step / (step_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    if prec == "f64":
+        roof = {"bound": "alu", "achieved": round(d_gflops, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": round(d_gflops / FP64_PEAK_GFLOPS, 4),
+                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s; no FP64 entry in MEASURED_PEAKS.json)",
+                "hbm_achieved_gbs": round(d_gbs, 1), "hbm_frac": round(d_gbs / peaks["hbm_gbs"], 4),
+                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
+    else:
+        roof = {"bound": "hbm", "achieved": round(d_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(d_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}
+    kkey = f"dslash_{prec}_r{args.recon}_{'x'.join(map(str, w['dims']))}_nrhs{nrhs}"
+    roof["traffic"] = recorded_traffic(kkey)
+    roof["kernel"] = f"wd::dslash_kernel<{pid},{args.recon},false,EpXpay> ({kkey})"
+    roof["algorithmic_bytes_per_launch"] = d_bytes
+    roof["algorithmic_flops_per_launch"] = FLOP_PER_SITE * V * nrhs
+    roof["avg_launch_ms"] = round(d_ms, 5)
+    roof["dslash_gflops"] = round(d_gflops, 2)
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if inner == "f64" else f"{inner}+f64", "data": "synthetic",
+            "config": config_of(args, w),
+            "cg": {"time_to_solution_ms": round(step_ms, 4), "iterations": iters,
+                   "reliable_updates": max(r["reliable_updates"] for r in results),
+                   "true_rel_resid": max(r["true_rel_resid"] for r in results),
+                   "operator_applications": n_apply},
+            "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+            "e2e": e2e}
+    if args.sweep:
+        line["dslash_sweep"] = sweep(wd, torch, flush, stream, args.recon)
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(w, U, b)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def sweep(wd, torch, flush, stream, recon):
+    from paper_1810_04201_gb300 import gen
+    out = {}
+    for L in (8, 12, 16, 24):
+        dims = (L, L, L, L)
+        lat = wd.Lattice(dims)
+        lat.set_gauge(gen.haar_links(dims, 3), recon=recon)
+        b = gen.gaussian_source(dims, 4)
+        row = {}
+        for prec, pid in (("f64", 0), ("f32", 1), ("f16", 2)):
+            fi = lat.pack(b, pid)
+            fo = lat.new_field(pid)
+            for _ in range(3):
+                lat.apply(0.12, fi, fo, pid)
+            ts = []
+            for _ in range(10):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lat.apply(0.12, fi, fo, pid)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.mean(ts)
+            V = lat.V
+            row[prec] = {"ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V / ms / 1e6, 1),
+                         "gbs": round(V * dslash_bytes(prec, recon) / ms / 1e6, 1)}
+        out[f"{L}^4"] = row
+        lat.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

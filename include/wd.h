@@ -1,0 +1,185 @@
+/*
+ * wd.h -- C ABI of the Wilson-Dirac operator library (libwd.so) for GB300 (sm_103a).
+ *
+ * The library applies the Wilson-Dirac operator of arXiv:1810.04201, section 2.1,
+ * Eq. (1), and solves D psi = eta (section 2.2, Eq. (4)) by Conjugate Gradient on
+ * the normal equations D^dag D x = D^dag b, with the whole solve on the device.
+ *
+ * Operator (hopping term written with -kappa; the paper prints +kappa, which is
+ * the same operator conjugated by eps(n) = (-1)^(x+y+z+t) on even lattices, so
+ * the paper's form is obtained by passing -kappa):
+ *
+ *   (D psi)(n) = psi(n) - kappa sum_mu [ b+_mu(n) (1 - gamma_mu) U_mu(n) psi(n+mu)
+ *                                      + b-_mu(n) (1 + gamma_mu) U_mu(n-mu)^dag psi(n-mu) ]
+ *
+ * gamma_mu are the matrices of the paper's Appendix A (the DeGrand-Rossi chiral
+ * basis); mu = 0, 1, 2, 3 = x, y, z, t.  With antiperiodic_t set, b+_3(n) = -1 when
+ * n_t = T-1 and b-_3(n) = -1 when n_t = 0 (section 2.3: periodic or antiperiodic
+ * boundary conditions); all other b are +1 and the stored links are never changed.
+ *
+ * Canonical layouts (the boundary format, complex = two doubles re, im):
+ *   links   U[mu][n][A][B]          4 x V x 3 x 3 complex128, row A, column B;
+ *                                    U_mu(n) on the edge n -> n+mu (section 2.1)
+ *   spinors psi[r][n][alpha][A]     nrhs x V x 4 x 3 complex128, spin-major,
+ *                                    colour-minor (su3_spinor, section 6.1)
+ *   site    n = x + Lx*(y + Ly*(z + Lz*t))
+ *
+ * Device fields.  The operators and solvers work on "fields": device buffers in
+ * the library's site-coalesced structure-of-arrays layout, of wd_field_bytes()
+ * bytes, written by wd_pack and read back by wd_unpack.  Per right-hand side:
+ *   WD_F64: 12 arrays (one per spin-colour component) of Vs complex128 (16 B);
+ *   WD_F32: 6 arrays of Vs float4 (two complex64 components each);
+ *   WD_F16: 3 arrays of Vs x 16 B (four half2 components each), then Vs floats
+ *           holding the per-site scale (the component of largest magnitude);
+ * where Vs is V rounded up to a multiple of 64.  Right-hand sides follow each
+ * other at a stride of wd_field_bytes(ctx, prec, 1).  Fields must be 256-byte
+ * aligned (torch and cudaMalloc allocations are).
+ *
+ * Ownership and streams.  The caller owns every field and canonical buffer; the
+ * context owns its gauge copies, its workspace and its CUDA graphs, and frees
+ * them in wd_destroy.  Every call is asynchronous on the context's stream, except
+ * the solvers, which wait for the result to fill wd_cg_result, and the calls
+ * whose on_device flag is 0 (host buffers), which return once the host buffer
+ * may be reused.
+ *
+ * Errors.  Every call returns a status and never aborts or throws.  Argument
+ * checks (null pointers, dimensions < 2, nrhs outside 1..WD_MAX_RHS, unknown
+ * precision, no gauge field set) happen before anything is launched; the message
+ * of the last failure is available from wd_last_error.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WD_MAX_RHS 16
+
+typedef enum wd_status {
+    WD_OK = 0,
+    WD_ERR_ARG = 1,           /* invalid argument; nothing was launched */
+    WD_ERR_CUDA = 2,          /* a CUDA call failed; see wd_last_error */
+    WD_ERR_OOM = 3,           /* device allocation failed */
+    WD_ERR_NOT_CONVERGED = 4, /* solver hit max_iter before the tolerance */
+    WD_ERR_BREAKDOWN = 5,     /* CG breakdown: p^dag A p <= 0 or a singular block Gram matrix */
+    WD_ERR_NONFINITE = 6,     /* a NaN or Inf appeared in a residual or scalar */
+    WD_ERR_TIMEOUT = 7,       /* a bounded device-side wait ran out (batched persistent solver) */
+    WD_ERR_STATE = 8          /* call out of order (e.g. no gauge field set) */
+} wd_status;
+
+typedef enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2 } wd_prec;
+
+typedef struct wd_ctx wd_ctx;
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice (dims[0..3], each >= 2) on the
+ * current CUDA device.  stream is a cudaStream_t (NULL = the legacy default stream);
+ * all work of this context is queued on it.  antiperiodic_t selects the antiperiodic
+ * time boundary (section 2.3). */
+wd_status wd_create(wd_ctx **ctx, const int dims[4], int antiperiodic_t, void *stream);
+wd_status wd_destroy(wd_ctx *ctx);
+wd_status wd_set_stream(wd_ctx *ctx, void *stream);
+
+/* Load the gauge field (section 2.3: the links stay resident across calls).
+ * U_canon: canonical links (4*V*9 complex128), host memory (on_device = 0) or device
+ * memory (on_device = 1).  recon = 18 stores all nine entries; recon = 12 stores the
+ * first two rows and rebuilds the third as conj(row0 x row1) (section 6.1, valid for
+ * SU(3) links only).  The lower-precision copies used by WD_F32/WD_F16 operators are
+ * derived from the same field when first needed. */
+wd_status wd_set_gauge(wd_ctx *ctx, const double *U_canon, int on_device, int recon);
+
+/* Bytes of one device field of nrhs right-hand sides in precision prec. */
+size_t wd_field_bytes(const wd_ctx *ctx, wd_prec prec, int nrhs);
+
+/* canonical (nrhs x V x 12 complex128, host or device) -> device field. */
+wd_status wd_pack(wd_ctx *ctx, const double *canon, int on_device, void *field, wd_prec prec, int nrhs);
+/* device field -> canonical (host or device). */
+wd_status wd_unpack(wd_ctx *ctx, const void *field, wd_prec prec, int nrhs, double *canon, int on_device);
+
+/* out = D in (section 2.1, Eq. (1)).  in and out are distinct fields of the same
+ * precision; gauge precision follows the field precision. */
+wd_status wd_apply(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
+/* out = D^dag in = gamma5 D gamma5 in (section 2.2, gamma5-hermiticity). */
+wd_status wd_apply_dagger(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
+/* out = D^dag D in (section 5: the product the paper moves to hardware).  Uses a
+ * context-owned temporary field. */
+wd_status wd_normal_apply(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
+
+/* Solver parameters.
+ *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side)
+ *   max_iter   iteration limit
+ *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16: mixed precision -- the Dslash
+ *              and the inner iteration in FP32 (or FP16 storage with FP32 arithmetic),
+ *              with FP64 reliable updates r = D^dag(b - D x) and the solution
+ *              accumulated in FP64
+ *   delta      reliable-update trigger: an update runs when the iterated residual
+ *              drops below delta times its maximum since the last update (0 = 0.1)
+ *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
+ *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
+ *              1: block CG (one Krylov space for all right-hand sides, FP64 only)
+ *   rhs_tile   right-hand sides per thread block in the multi-RHS Dslash (0 = tuned) */
+typedef struct wd_cg_params {
+    double tol;
+    int max_iter;
+    int inner_prec;
+    double delta;
+    int nrhs;
+    int block;
+    int rhs_tile;
+} wd_cg_params;
+
+/* Per right-hand side result. */
+typedef struct wd_cg_result {
+    int iters;               /* CG iterations */
+    int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
+    double true_rel_resid;   /* ||D^dag(b - D x)|| / ||D^dag b||, recomputed in FP64 at the end */
+    double true_rel_resid_b; /* ||b - D x|| / ||b||, recomputed in FP64 at the end */
+    double seconds;          /* device time of the solve */
+    int status;              /* wd_status of this right-hand side */
+} wd_cg_result;
+
+/* Solve D x = b for nrhs right-hand sides by CG on D^dag D x = D^dag b, entirely on
+ * the device (a CUDA graph with a device-side loop).  b, x: WD_F64 fields of
+ * params->nrhs right-hand sides; x holds the initial guess on entry (zeros for the
+ * default start; section 2.2, psi <- psi_0) and the solution on exit.  result points
+ * to params->nrhs results.  Returns WD_OK when every right-hand side converged. */
+wd_status wd_cg_solve(wd_ctx *ctx, double kappa, const void *b, void *x, const wd_cg_params *params,
+                      wd_cg_result *result);
+
+/* The same solve on canonical buffers (nrhs x V x 12 complex128) in host memory
+ * (on_device = 0; pinned memory gives asynchronous copies) or device memory: packs b
+ * and x, solves, unpacks x.  This is the end-to-end call. */
+wd_status wd_cg_solve_canonical(wd_ctx *ctx, double kappa, const double *b_canon, double *x_canon, int on_device,
+                                const wd_cg_params *params, wd_cg_result *result);
+
+/* Solve n independent lattices, each with its own context (dims, gauge field) and
+ * kappa, in one persistent cooperative kernel launch, with mixed-precision
+ * (inner_prec) CG and FP64 reliable updates.  All contexts must live on the same
+ * device; the work runs on ctxs[0]'s stream.  b[i], x[i]: WD_F64 fields of ctxs[i]
+ * (one right-hand side); result[i] receives lattice i's result.  Grid-wide waits
+ * inside the kernel are bounded; when one runs out, every result gets
+ * WD_ERR_TIMEOUT and the kernel returns. */
+wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const void *const *b, void *const *x,
+                              int n, const wd_cg_params *params, wd_cg_result *result);
+
+/* Autotuner: time the site-tile (threads per block) and right-hand-side-tile
+ * choices of the Dslash for this context's lattice, precision and nrhs, and keep
+ * the fastest for later calls.  Writes the choice to *site_tile and *rhs_tile
+ * (either may be NULL).  Uses context-owned scratch fields; synchronises the stream. */
+wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
+/* Fix the tile choice by hand (site_tile in {32, 64, 128, 256}; rhs_tile >= 1). */
+wd_status wd_set_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int site_tile, int rhs_tile);
+
+/* Launch-configuration query: number of kernel launches the last wd_* call queued
+ * (graph kernel nodes count once per execution). */
+long long wd_kernel_launches(const wd_ctx *ctx);
+
+const char *wd_status_string(wd_status s);
+const char *wd_last_error(const wd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WD_H */

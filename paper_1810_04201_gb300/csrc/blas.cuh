@@ -1,0 +1,164 @@
+// Element-wise and layout kernels: pack/unpack, gauge upload, precision
+// conversion and the CG vector updates (sm_103a).  One thread per (site,
+// right-hand side); rows (right-hand sides) can be masked by the per-RHS solver
+// state: mask 0 = every row, 1 = rows still iterating, 2 = rows with a reliable
+// update pending.
+#pragma once
+#include "wd_internal.cuh"
+
+namespace wd {
+
+struct VecArgs {
+    int V, Vs, nrhs;
+    const void *a; size_t a_stride;
+    void *b; size_t b_stride;
+    const void *c; size_t c_stride;
+    Scalars *sc;
+    int mask;
+    unsigned long long cond;   // while-loop handle to set (0 = none)
+    int *state;                // [0] body iterations, [1] reliable-update bodies run
+};
+
+template <class T> __device__ __forceinline__ const void *rp(const T *b, size_t st, int r) {
+    return reinterpret_cast<const char *>(b) + st * (size_t)r;
+}
+template <class T> __device__ __forceinline__ void *rp(T *b, size_t st, int r) {
+    return reinterpret_cast<char *>(b) + st * (size_t)r;
+}
+
+// canonical (nrhs x V x 12 complex128) -> field of precision P
+template <int P> __global__ void k_pack(VecArgs v) {
+    using R = typename Real<P>::T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (s >= v.V) return;
+    const double2 *src = reinterpret_cast<const double2 *>(v.a) + ((size_t)r * v.V + s) * 12;
+    C<R> x[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) { double2 t = src[c]; x[c] = C<R>{R(t.x), R(t.y)}; }
+    SpinorIO<P>::store(rp(v.b, v.b_stride, r), v.Vs, s, x);
+}
+
+// field of precision P -> canonical
+template <int P> __global__ void k_unpack(VecArgs v) {
+    using R = typename Real<P>::T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (s >= v.V) return;
+    C<R> x[12];
+    SpinorIO<P>::load(rp(v.a, v.a_stride, r), v.Vs, s, x);
+    double2 *dst = reinterpret_cast<double2 *>(v.b) + ((size_t)r * v.V + s) * 12;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)x[c].re, (double)x[c].im);
+}
+
+// b (precision PB) = a (precision PA), masked rows
+template <int PA, int PB> __global__ void k_convert(VecArgs v) {
+    using RA = typename Real<PA>::T;
+    using RB = typename Real<PB>::T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
+    C<RA> x[12];
+    C<RB> y[12];
+    SpinorIO<PA>::load(rp(v.a, v.a_stride, r), v.Vs, s, x);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y[c] = C<RB>{RB(x[c].re), RB(x[c].im)};
+    SpinorIO<PB>::store(rp(v.b, v.b_stride, r), v.Vs, s, y);
+}
+
+// p = r + beta p   (p, r in precision P), rows still iterating.  Block (0, 0)
+// thread 0 counts the iteration and sets the while-loop condition (any row active);
+// thread 0 of every x-block-0 clears the row's pending reliable-update flag.
+template <int P> __global__ void k_xpby(VecArgs v) {
+    using R = typename Real<P>::T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (v.cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        int any = 0, cap = 0;
+        for (int k = 0; k < v.nrhs; ++k) {
+            any |= v.sc[k].active;
+            cap = cap > v.sc[k].max_iter ? cap : v.sc[k].max_iter;
+        }
+        int body = 1;
+        if (v.state) body = (v.state[0] += 1);
+        if (body > cap + 2) any = 0;  // hard stop: the loop never outlives max_iter
+        cudaGraphSetConditional((cudaGraphConditionalHandle)v.cond, any ? 1u : 0u);
+    }
+    if (v.sc && blockIdx.x == 0 && threadIdx.x == 0 && r < v.nrhs) v.sc[r].do_update = 0;
+    if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
+    const R beta = R(v.sc[r].beta);
+    C<R> x[12], y[12];
+    SpinorIO<P>::load(rp(v.a, v.a_stride, r), v.Vs, s, x);  // r
+    void *pb = rp(v.b, v.b_stride, r);
+    SpinorIO<P>::load(pb, v.Vs, s, y);                       // p
+#pragma unroll
+    for (int c = 0; c < 12; ++c) y[c] = C<R>{x[c].re + beta * y[c].re, x[c].im + beta * y[c].im};
+    SpinorIO<P>::store(pb, v.Vs, s, y);
+}
+
+// x (F64) += xs (F32); xs = 0, rows with a pending reliable update.  Block (0, 0)
+// thread 0 counts the reliable-update bodies run.
+template <int DUMMY = 0> __global__ void k_reliable_x(VecArgs v) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (v.state && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) v.state[1] += 1;
+    if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
+    C<double> x[12];
+    C<float> xs[12];
+    void *xb = rp(v.b, v.b_stride, r);
+    void *sb = const_cast<void *>(rp(v.a, v.a_stride, r));
+    SpinorIO<F64>::load(xb, v.Vs, s, x);
+    SpinorIO<F32>::load(sb, v.Vs, s, xs);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        x[c] = C<double>{x[c].re + (double)xs[c].re, x[c].im + (double)xs[c].im};
+        xs[c] = C<float>{0.f, 0.f};
+    }
+    SpinorIO<F64>::store(xb, v.Vs, s, x);
+    SpinorIO<F32>::store(sb, v.Vs, s, xs);
+}
+
+// field = 0 (precision P), every row
+template <int P> __global__ void k_zero(VecArgs v) {
+    using R = typename Real<P>::T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (s >= v.V) return;
+    C<R> z[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) z[c] = C<R>{R(0), R(0)};
+    SpinorIO<P>::store(rp(v.b, v.b_stride, r), v.Vs, s, z);
+}
+
+// gauge: canonical (4 x V x 9 complex128, device) -> field of precision P, recon R
+template <int P, int RECON> __global__ void k_gauge_pack(const double2 *canon, void *dst, int V, int Vs,
+                                                         size_t dir_bytes) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, mu = blockIdx.y;
+    if (s >= V) return;
+    const double2 *u = canon + ((size_t)mu * V + s) * 9;
+    char *base = reinterpret_cast<char *>(dst) + (size_t)mu * dir_bytes;
+    constexpr int n = RECON == 12 ? 6 : 9;
+    if (P == F64) {
+        double2 *d = reinterpret_cast<double2 *>(base) + s;
+        for (int e = 0; e < n; ++e) d[(size_t)e * Vs] = u[e];
+    } else if (P == F32) {
+        float4 *d = reinterpret_cast<float4 *>(base) + s;
+        const int n4 = n / 2;
+        for (int j = 0; j < n4; ++j)
+            d[(size_t)j * Vs] = make_float4((float)u[2 * j].x, (float)u[2 * j].y, (float)u[2 * j + 1].x, (float)u[2 * j + 1].y);
+        if (RECON == 18) {
+            float2 *e = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(base) + (size_t)4 * Vs) + s;
+            *e = make_float2((float)u[8].x, (float)u[8].y);
+        }
+    } else {
+        uint4 *d = reinterpret_cast<uint4 *>(base) + s;
+        auto h = [&](int e) { return f2h((float)u[e].x, (float)u[e].y); };
+        if (RECON == 12) {
+            *d = make_uint4(h(0), h(1), h(2), h(3));
+            uint2 *e = reinterpret_cast<uint2 *>(reinterpret_cast<uint4 *>(base) + Vs) + s;
+            *e = make_uint2(h(4), h(5));
+        } else {
+            d[0] = make_uint4(h(0), h(1), h(2), h(3));
+            d[Vs] = make_uint4(h(4), h(5), h(6), h(7));
+            uint32_t *e = reinterpret_cast<uint32_t *>(reinterpret_cast<uint4 *>(base) + (size_t)2 * Vs) + s;
+            *e = h(8);
+        }
+    }
+}
+
+}  // namespace wd

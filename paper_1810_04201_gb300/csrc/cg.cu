@@ -1,0 +1,390 @@
+// Device-resident CG on the normal equations (section 2.2), FP64 and mixed
+// precision with FP64 reliable updates, for one or many right-hand sides.
+//
+// The whole solve is one CUDA graph: setup kernels, a conditional WHILE node
+// whose body is one CG step (three kernels; the mixed-precision body adds a
+// conditional IF node holding the reliable update), and the final FP64
+// true-residual check.  The loop condition is set on the device, so the host
+// waits only once, for the result.
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "cg_kernels.cuh"
+#include "wd_host.h"
+
+using namespace wd;
+
+namespace wd {
+
+// ------------------------------------------------------------------ graph builder
+struct GraphBuilder {
+    cudaGraph_t g;
+    std::vector<cudaGraphNode_t> deps;
+    cudaError_t err = cudaSuccess;
+    long long nkernels = 0;
+
+    explicit GraphBuilder(cudaGraph_t graph) : g(graph) {}
+
+    template <class Arg>
+    void kernel(void (*f)(Arg), dim3 grid, dim3 block, const Arg &arg) {
+        if (err != cudaSuccess) return;
+        Arg copy = arg;
+        void *params[1] = {&copy};
+        cudaKernelNodeParams p{};
+        p.func = (void *)f;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = 0;
+        p.kernelParams = params;
+        cudaGraphNode_t n;
+        err = cudaGraphAddKernelNode(&n, g, deps.data(), deps.size(), &p);
+        if (err == cudaSuccess) deps.assign(1, n);
+        ++nkernels;
+    }
+
+    // Appends a conditional node; returns its body graph.
+    cudaGraph_t conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+        if (err != cudaSuccess) return nullptr;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        cudaGraphNode_t n;
+        err = cudaGraphAddNode(&n, g, deps.data(), nullptr, deps.size(), &np);
+        if (err != cudaSuccess) return nullptr;
+        deps.assign(1, n);
+        return np.conditional.phGraph_out[0];
+    }
+};
+
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Grid for a reducing Dslash: at most the blocks that fit on the machine at once.
+template <class K>
+static dim3 reduce_grid(K kernel, const Geom &g, DslashTiles t, int nrhs) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, t.site_tile * t.rhs_tile, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int need = (g.V + t.site_tile - 1) / t.site_tile;
+    int cap = per_sm * num_sms();
+    return dim3(need < cap ? need : cap, (nrhs + t.rhs_tile - 1) / t.rhs_tile);
+}
+
+struct Fields {
+    void *b, *x, *db, *r, *p, *t;      // FP64
+    void *rs, *ps, *ts, *xs;            // inner precision (xs FP32)
+    Scalars *sc;
+    double *partial;
+    unsigned *counter;
+    int *state;
+};
+
+template <int P, int RECON, bool DAG, class Ep>
+static void add_dslash(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool reduce) {
+    auto k = dslash_kernel<P, RECON, DAG, Ep>;
+    dim3 block(t.site_tile, t.rhs_tile);
+    dim3 grid = reduce ? reduce_grid(k, a.g, t, a.nrhs)
+                       : dim3((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    gb.kernel(k, grid, block, a);
+}
+
+template <class K>
+static void add_vec(GraphBuilder &gb, K k, const VecArgs &v) {
+    gb.kernel(k, dim3((v.V + 127) / 128, v.nrhs), dim3(128), v);
+}
+
+struct SolverPlan {
+    int recon;
+    double kappa;
+    int nrhs;
+    Prec inner;
+    DslashTiles t64, tin;
+};
+
+// Build the FP64 (inner == F64) or mixed-precision solver graph.
+template <int RECON, int SP>
+static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                               cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    cudaGraph_t graph;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    GraphBuilder gb(graph);
+    const size_t s64 = spinor_bytes(F64, c->g.Vs), sin = spinor_bytes((Prec)SP, c->g.Vs),
+                 s32 = spinor_bytes(F32, c->g.Vs);
+    const bool mixed = SP != F64;
+
+    DslashArgs base{};
+    base.g = c->g;
+    base.gauge = g64;
+    base.gauge_dir = gauge_dir_bytes(c, F64);
+    base.kappa = pl.kappa;
+    base.nrhs = pl.nrhs;
+    base.sc = f.sc;
+    base.partial = f.partial;
+    base.counter = f.counter;
+    base.state = f.state;
+    base.in_stride = base.out_stride = base.a0_stride = base.a1_stride = base.a2_stride = base.a3_stride = s64;
+
+    VecArgs vb{};
+    vb.V = c->g.V;
+    vb.Vs = c->g.Vs;
+    vb.nrhs = pl.nrhs;
+    vb.sc = f.sc;
+    vb.state = f.state;
+
+    // ---- setup (FP64): db = D^dag b; t = D x0; r = db - D^dag t; p = r
+    {
+        DslashArgs a = base;
+        a.mask = 0;
+        a.in = f.b; a.out = f.db;
+        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+        a.in = f.x; a.out = f.t;
+        add_dslash<F64, RECON, false, EpXpay>(gb, a, pl.t64, false);
+        a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
+        add_dslash<F64, RECON, true, EpSetupR>(gb, a, pl.t64, true);
+    }
+    long long n_setup = gb.nkernels;
+    if (mixed) {
+        VecArgs v = vb;
+        v.mask = 0;
+        v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
+        add_vec(gb, k_convert<F64, SP>, v);
+        v.b = f.ps;
+        add_vec(gb, k_convert<F64, SP>, v);
+        v.b = f.xs; v.b_stride = s32;
+        add_vec(gb, k_zero<F32>, v);
+        n_setup = gb.nkernels;
+    }
+
+    // ---- loop
+    cudaGraphConditionalHandle hwhile = 0, hif = 0;
+    if (gb.err == cudaSuccess) gb.err = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = gb.conditional(hwhile, cudaGraphCondTypeWhile);
+    long long n_body = 0, n_if = 0;
+    if (gb.err == cudaSuccess) {
+        GraphBuilder bb(body);
+        if (!mixed) {
+            DslashArgs a = base;
+            a.mask = 1;
+            a.in = f.p; a.out = f.t;
+            add_dslash<F64, RECON, false, EpCG1>(bb, a, pl.t64, true);
+            a.in = f.t; a.a0 = f.p; a.a1 = f.r; a.a2 = f.x;
+            add_dslash<F64, RECON, true, EpCG2>(bb, a, pl.t64, true);
+            VecArgs v = vb;
+            v.mask = 1;
+            v.a = f.r; v.a_stride = s64; v.b = f.p; v.b_stride = s64; v.cond = hwhile;
+            add_vec(bb, k_xpby<F64>, v);
+        } else {
+            if (bb.err == cudaSuccess) bb.err = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
+            DslashArgs a = base;
+            a.mask = 1;
+            a.gauge = gin;
+            a.gauge_dir = gauge_dir_bytes(c, (Prec)SP);
+            a.in_stride = a.out_stride = a.a0_stride = a.a1_stride = sin;
+            a.a2_stride = s32;
+            a.in = f.ps; a.out = f.ts;
+            add_dslash<SP, RECON, false, EpCG1>(bb, a, pl.tin, true);
+            a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
+            add_dslash<SP, RECON, true, EpCG2Mixed>(bb, a, pl.tin, true);
+            cudaGraph_t ifb = bb.conditional(hif, cudaGraphCondTypeIf);
+            if (bb.err == cudaSuccess) {
+                GraphBuilder ib(ifb);
+                VecArgs v = vb;
+                v.mask = 2;
+                v.a = f.xs; v.a_stride = s32; v.b = f.x; v.b_stride = s64;
+                add_vec(ib, k_reliable_x<0>, v);
+                DslashArgs r = base;
+                r.mask = 2;
+                r.in = f.x; r.out = f.t;
+                add_dslash<F64, RECON, false, EpXpay>(ib, r, pl.t64, false);
+                r.in = f.t; r.a0 = f.db; r.a1 = f.r;
+                add_dslash<F64, RECON, true, EpReliable>(ib, r, pl.t64, true);
+                v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
+                add_vec(ib, k_convert<F64, SP>, v);
+                bb.err = ib.err;
+                n_if = ib.nkernels;
+            }
+            VecArgs v = vb;
+            v.mask = 1;
+            v.a = f.rs; v.a_stride = sin; v.b = f.ps; v.b_stride = sin; v.cond = hwhile;
+            add_vec(bb, k_xpby<SP>, v);
+        }
+        gb.err = bb.err;
+        n_body = bb.nkernels;
+    }
+
+    // ---- final FP64 check: t = D x, |b - t|^2; |db - D^dag t|^2
+    {
+        DslashArgs a = base;
+        a.mask = 0;
+        a.in = f.x; a.out = f.t; a.a0 = f.b;
+        add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
+        a.in = f.t; a.a0 = f.db;
+        add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
+    }
+    const long long n_final = 2;
+    e = gb.err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    counts = {n_setup, n_body, n_if, n_final};
+    return e;
+}
+
+template <int RECON>
+static cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                             cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    switch (pl.inner) {
+    case F64: return build_graph<RECON, F64>(c, pl, f, g64, gin, exec, counts);
+    case F32: return build_graph<RECON, F32>(c, pl, f, g64, gin, exec, counts);
+    default: return build_graph<RECON, F16>(c, pl, f, g64, gin, exec, counts);
+    }
+}
+
+wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm,
+                         wd_cg_result *res);
+
+}  // namespace wd
+
+extern "C" {
+
+wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm, wd_cg_result *res) {
+    if (!c) return WD_ERR_ARG;
+    c->launches = 0;
+    if (!b || !x || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve: null argument");
+    const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;
+    if (nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_cg_solve: nrhs above WD_MAX_RHS");
+    if (prm->inner_prec < 0 || prm->inner_prec > 2) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad inner_prec");
+    if (!(prm->tol > 0) || !std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad tol or kappa");
+    if (b == x) return fail(c, WD_ERR_ARG, "wd_cg_solve: b and x must be distinct");
+    if (prm->block) {
+        if (prm->inner_prec != WD_F64) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG runs in FP64 only");
+        return block_cg_solve(c, kappa, b, x, prm, res);
+    }
+    const Prec inner = (Prec)prm->inner_prec;
+    const void *g64, *gin;
+    wd_status s = gauge_get(c, F64, &g64);
+    if (s != WD_OK) return s;
+    s = gauge_get(c, inner, &gin);
+    if (s != WD_OK) return s;
+
+    const size_t s64 = spinor_bytes(F64, c->g.Vs) * nrhs;
+    Fields f{};
+    const char *n64[6] = {"cg_b", "cg_x", "cg_db", "cg_r", "cg_p", "cg_t"};
+    void **p64[6] = {&f.b, &f.x, &f.db, &f.r, &f.p, &f.t};
+    for (int i = 0; i < 6; ++i)
+        if ((s = ws_get(c, n64[i], s64, p64[i])) != WD_OK) return s;
+    if (inner != F64) {
+        const size_t sin = spinor_bytes(inner, c->g.Vs) * nrhs;
+        std::string sfx = inner == F32 ? "32" : "16";
+        if ((s = ws_get(c, "cg_rs" + sfx, sin, &f.rs)) != WD_OK) return s;
+        if ((s = ws_get(c, "cg_ps" + sfx, sin, &f.ps)) != WD_OK) return s;
+        if ((s = ws_get(c, "cg_ts" + sfx, sin, &f.ts)) != WD_OK) return s;
+        if ((s = ws_get(c, "cg_xs", spinor_bytes(F32, c->g.Vs) * nrhs, &f.xs)) != WD_OK) return s;
+    }
+    void *tmp;
+    if ((s = ws_get(c, "cg_scalars", sizeof(Scalars) * WD_MAX_RHS, &tmp)) != WD_OK) return s;
+    f.sc = (Scalars *)tmp;
+    const size_t npart = (size_t)WD_MAX_RHS * 3 * 8192;
+    if ((s = ws_get(c, "partial", npart * sizeof(double), &tmp)) != WD_OK) return s;
+    f.partial = (double *)tmp;
+    if ((s = ws_get(c, "counter", 256, &tmp)) != WD_OK) return s;
+    f.counter = (unsigned *)tmp;
+    f.state = (int *)((char *)tmp + 64);
+
+    SolverPlan pl{c->recon, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs)};
+    char key[256];
+    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
+             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile);
+    cudaGraphExec_t exec;
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        std::vector<long long> counts;
+        cudaError_t e = c->recon == 12 ? build_for<12>(c, pl, f, g64, gin, &exec, counts)
+                                       : build_for<18>(c, pl, f, g64, gin, &exec, counts);
+        if (e != cudaSuccess) return cuda_fail(c, e, "building the CG graph");
+        c->graphs[key] = exec;
+        c->graph_info[key] = counts;
+        WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 256, c->stream));
+    } else {
+        exec = (cudaGraphExec_t)it->second;
+    }
+
+    // per-RHS state
+    std::vector<Scalars> h(nrhs);
+    const double delta = prm->delta > 0 ? prm->delta : 0.1;
+    for (int r = 0; r < nrhs; ++r) {
+        std::memset(&h[r], 0, sizeof(Scalars));
+        h[r].tol2 = prm->tol * prm->tol;
+        h[r].max_iter = prm->max_iter;
+        h[r].delta2 = delta * delta;
+        h[r].active = 1;
+        h[r].status = WD_ERR_NOT_CONVERGED;
+    }
+    WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
+    WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
+    WD_CUDA(c, cudaMemcpyAsync(f.b, b, s64, cudaMemcpyDeviceToDevice, c->stream));
+    WD_CUDA(c, cudaMemcpyAsync(f.x, x, s64, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t e0, e1;
+    WD_CUDA(c, cudaEventCreate(&e0));
+    WD_CUDA(c, cudaEventCreate(&e1));
+    WD_CUDA(c, cudaEventRecord(e0, c->stream));
+    WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
+    WD_CUDA(c, cudaEventRecord(e1, c->stream));
+    WD_CUDA(c, cudaMemcpyAsync(x, f.x, s64, cudaMemcpyDeviceToDevice, c->stream));
+    WD_CUDA(c, cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream));
+    int st[2];
+    WD_CUDA(c, cudaMemcpyAsync(st, f.state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const std::vector<long long> &cnt = c->graph_info[key];
+    c->launches = cnt[0] + (long long)st[0] * cnt[1] + (long long)st[1] * cnt[2] + cnt[3];
+
+    wd_status worst = WD_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        res[r].iters = h[r].iter;
+        res[r].reliable_updates = h[r].reliable;
+        res[r].true_rel_resid = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
+        res[r].true_rel_resid_b = h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2);
+        res[r].seconds = ms * 1e-3;
+        res[r].status = h[r].status;
+        if (h[r].status != WD_OK && worst == WD_OK) worst = (wd_status)h[r].status;
+    }
+    if (worst != WD_OK) c->last_error = std::string("wd_cg_solve: ") + wd_status_string(worst);
+    return worst;
+}
+
+wd_status wd_cg_solve_canonical(wd_ctx *c, double kappa, const double *b_canon, double *x_canon, int on_device,
+                                const wd_cg_params *prm, wd_cg_result *res) {
+    if (!c) return WD_ERR_ARG;
+    if (!b_canon || !x_canon || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve_canonical: null argument");
+    const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;
+    if (nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_cg_solve_canonical: nrhs above WD_MAX_RHS");
+    const size_t fb = spinor_bytes(F64, c->g.Vs) * nrhs;
+    void *bf, *xf;
+    wd_status s;
+    if ((s = ws_get(c, "canon_b", fb, &bf)) != WD_OK) return s;
+    if ((s = ws_get(c, "canon_x", fb, &xf)) != WD_OK) return s;
+    if ((s = wd_pack(c, b_canon, on_device, bf, WD_F64, nrhs)) != WD_OK) return s;
+    if ((s = wd_pack(c, x_canon, on_device, xf, WD_F64, nrhs)) != WD_OK) return s;
+    wd_status sol = wd_cg_solve(c, kappa, bf, xf, prm, res);
+    const long long l = c->launches;
+    if (sol != WD_OK && sol != WD_ERR_NOT_CONVERGED && sol != WD_ERR_BREAKDOWN && sol != WD_ERR_NONFINITE) return sol;
+    if ((s = wd_unpack(c, xf, WD_F64, nrhs, x_canon, on_device)) != WD_OK) return s;
+    c->launches = l + 4;
+    return sol;
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+// Dslash epilogues of the CG solvers: the vector updates and reductions of one CG
+// step are fused into the operator kernel that produces their input, and the
+// scalar recursion (alpha, beta, stopping test) runs in the last block to finish.
+//
+// CG on the normal equations (section 2.2; Hestenes-Stiefel with squared norms):
+//   setup  db = D^dag b, t = D x0, r = db - D^dag t, p = r, rho = |r|^2
+//   step   t = D p;            alpha = rho / |t|^2              (EpCG1)
+//          q = D^dag t; r -= alpha q; x += alpha p; rho' = |r|^2 (EpCG2 / EpCG2Mixed)
+//          beta = rho' / rho; p = r + beta p                     (k_xpby)
+//   stop   |r|^2 <= tol^2 |D^dag b|^2
+// Mixed precision: the step runs on low-precision fields (p, t, r in the inner
+// precision, the partial solution xs in FP32); when |r|^2 drops below delta^2
+// times its value at the last update (or below the tolerance), a reliable update
+// runs in FP64: x += xs, xs = 0, r = D^dag (b - D x), rho = |r|^2, and r is
+// copied back to the inner precision.
+#pragma once
+#include "dslash.cuh"
+#include "blas.cuh"
+
+namespace wd {
+
+// Block + grid reduction of NV doubles per row; `fin(row, tot)` runs once per
+// enabled row, in thread (0, 0) of the last block, rows in order.
+template <int NV, class F>
+__device__ __forceinline__ bool reduce_finish(const DslashArgs &a, double (&v)[NV], F &&fin) {
+    __shared__ double smem[WD_MAX_RHS * 8 * NV];
+    __shared__ double tot[WD_MAX_RHS * NV];
+    block_reduce_rows<NV>(v, smem);
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (threadIdx.x == 0 && r < a.nrhs)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a.partial[((size_t)r * NV + k) * gridDim.x + blockIdx.x] = v[k];
+    const bool last = last_block(a.counter);
+    if (last) {
+        sum_partials<NV>(a.partial, gridDim.x, a.nrhs, tot);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            for (int row = 0; row < a.nrhs; ++row)
+                if (row_on(a.sc, a.mask, row)) fin(row, tot + row * NV);
+            *a.counter = 0;
+        }
+    }
+    return last;
+}
+
+__device__ __forceinline__ bool is_fin(double x) { return isfinite(x); }
+
+template <class R> __device__ __forceinline__ void xpay_site(C<R> (&p)[12], const C<R> (&acc)[12], R k) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
+}
+
+// db = D^dag b (out); |db|^2 -> rhs2, |b|^2 -> b2, tol2 *= rhs2
+struct EpSetupDb {
+    struct State { double v[2]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> p[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, p);
+        st.v[1] += norm2_of(p);
+        xpay_site(p, acc, R(a.kappa));
+        st.v[0] += norm2_of(p);
+        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<2>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            c.rhs2 = t[0];
+            c.b2 = t[1];
+            c.tol2 *= t[0];
+        });
+    }
+};
+
+// q = D^dag t; r = db - q (a1), p = r (a2); rho = |r|^2; rows already converged stop
+struct EpSetupR {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> q[12], d[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        st.v[0] += norm2_of(d);
+        SpinorIO<P>::store(rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
+        SpinorIO<P>::store(rhs_ptr<R>(a.a2, a.a2_stride, r), a.g.Vs, s, d);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            c.rho = t[0];
+            c.rmax2 = t[0];
+            c.iter = 0;
+            if (!is_fin(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; }
+            else if (t[0] <= c.tol2) { c.status = WD_OK; c.active = 0; }
+            else if (c.max_iter <= 0) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+        });
+    }
+};
+
+// t = D p (out); pAp = |t|^2; alpha = rho / pAp
+struct EpCG1 {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> p[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, p);
+        xpay_site(p, acc, R(a.kappa));
+        st.v[0] += norm2_of(p);
+        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            c.pAp = t[0];
+            if (!is_fin(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; c.alpha = 0.0; }
+            else if (!(t[0] > 0.0)) { c.status = WD_ERR_BREAKDOWN; c.active = 0; c.alpha = 0.0; }
+            else c.alpha = c.rho / t[0];
+        });
+    }
+};
+
+// FP64 step: q = D^dag t; r -= alpha q (a1); x += alpha p (a2, p = a0); rho' = |r|^2
+struct EpCG2 {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        const R alpha = R(a.sc[r].alpha);
+        C<R> q[12], v[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        void *rr = rhs_ptr<R>(a.a1, a.a1_stride, r);
+        SpinorIO<P>::load(rr, a.g.Vs, s, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
+        st.v[0] += norm2_of(v);
+        SpinorIO<P>::store(rr, a.g.Vs, s, v);
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
+        void *xr = rhs_ptr<R>(a.a2, a.a2_stride, r);
+        SpinorIO<P>::load(xr, a.g.Vs, s, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re + alpha * q[c].re, v[c].im + alpha * q[c].im};
+        SpinorIO<P>::store(xr, a.g.Vs, s, v);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            const double rn = t[0];
+            c.iter += 1;
+            c.rho_new = rn;
+            if (!is_fin(rn)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+            c.beta = rn / c.rho;
+            c.rho = rn;
+            if (rn <= c.tol2) { c.status = WD_OK; c.active = 0; }
+            else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+        });
+    }
+};
+
+// Mixed step (inner precision P): q = D^dag t; r -= alpha q (a1, P); xs += alpha p
+// (a2, FP32; p = a0, P); rho' = |r|^2.  Decides the reliable update and sets the
+// if-condition (cond) when any row needs one.
+struct EpCG2Mixed {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        const R alpha = R(a.sc[r].alpha);
+        C<R> q[12], v[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        void *rr = rhs_ptr<R>(a.a1, a.a1_stride, r);
+        SpinorIO<P>::load(rr, a.g.Vs, s, v);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
+        st.v[0] += norm2_of(v);
+        SpinorIO<P>::store(rr, a.g.Vs, s, v);
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
+        C<float> xs[12];
+        void *xr = rhs_ptr<R>(a.a2, a.a2_stride, r);
+        SpinorIO<F32>::load(xr, a.g.Vs, s, xs);
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            xs[c] = C<float>{xs[c].re + float(alpha * q[c].re), xs[c].im + float(alpha * q[c].im)};
+        SpinorIO<F32>::store(xr, a.g.Vs, s, xs);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        __shared__ int any;
+        if (threadIdx.x == 0 && threadIdx.y == 0) any = 0;
+        const bool last = reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            const double rn = t[0];
+            c.iter += 1;
+            c.rho_new = rn;
+            if (!is_fin(rn)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+            if (c.iter > c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; return; }
+            if (rn <= c.tol2 || rn < c.delta2 * c.rmax2 || c.iter >= c.max_iter) {
+                c.do_update = 1;
+                any = 1;
+            } else {
+                c.beta = rn / c.rho;
+                c.rho = rn;
+                c.rmax2 = fmax(c.rmax2, rn);
+            }
+        });
+        // the if-condition keeps its value across loop iterations: set it every time
+        if (last && a.cond && threadIdx.x == 0 && threadIdx.y == 0)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, any ? 1u : 0u);
+    }
+};
+
+// Reliable update, FP64: q = D^dag t (t = D x); r = db - q (a1, db = a0); rho = |r|^2
+struct EpReliable {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> q[12], d[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        st.v[0] += norm2_of(d);
+        SpinorIO<P>::store(rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            const double rt = t[0];
+            c.reliable += 1;
+            if (!is_fin(rt)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+            c.beta = rt / c.rho;
+            c.rho = rt;
+            c.rmax2 = rt;
+            if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
+            else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+        });
+    }
+};
+
+// Final check, pass 1: t = D x (out); |b - t|^2 -> true_b2 (b = a0)
+struct EpTrue1 {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> p[12], b[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, p);
+        xpay_site(p, acc, R(a.kappa));
+        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, b);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) b[c] = csub(b[c], p[c]);
+        st.v[0] += norm2_of(b);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) { a.sc[row].true_b2 = t[0]; });
+    }
+};
+
+// Final check, pass 2: q = D^dag t; |db - q|^2 -> true_n2 (db = a0)
+struct EpTrue2 {
+    struct State { double v[1]; };
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &st) {
+        C<R> q[12], d[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        st.v[0] += norm2_of(d);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) { a.sc[row].true_n2 = t[0]; });
+    }
+};
+
+}  // namespace wd

@@ -1,0 +1,200 @@
+// Wilson-Dirac hopping term and the Dslash kernel template (sm_103a).
+//
+// One thread computes one output site of one right-hand side.  A thread block is
+// (site_tile x rhs_tile) threads: the rhs_tile right-hand sides of a block read
+// the same links, which the L1 cache then serves once per block.
+//
+// Per hop (section 2.1, Eq. (1) and Eq. (3); section 2.1, half-spinor remark):
+//   gamma_mu = [[0, A_mu], [A_mu^dag, 0]] in 2x2 spin blocks (Appendix A), with
+//   A_0 = [[0, i], [i, 0]], A_1 = [[0, -1], [1, 0]], A_2 = [[i, 0], [0, -i]], A_3 = 1.
+//   (1 + s gamma_mu) psi has upper half h = psi_up + s A_mu psi_dn and lower half
+//   s A_mu^dag h, so only the two upper colour vectors are multiplied by the link:
+//   spin projection -> SU(3) x 2 colour vectors -> reconstruction -> accumulation.
+//   D: forward hop s = -1 with U_mu(n), backward hop s = +1 with U_mu(n-mu)^dag.
+//   D^dag: the signs swap (gamma5 D gamma5 = D^dag, section 2.2).
+//   Antiperiodic time boundary: the hop across t = T-1 <-> 0 is multiplied by -1.
+#pragma once
+#include "wd_internal.cuh"
+
+namespace wd {
+
+struct DslashArgs {
+    Geom g;
+    const void *in;
+    size_t in_stride;   // bytes between right-hand sides
+    void *out;
+    size_t out_stride;
+    const void *gauge;
+    size_t gauge_dir;   // bytes between directions
+    double kappa;
+    int nrhs;
+    // epilogue operands (meaning depends on the epilogue)
+    const void *a0; size_t a0_stride;
+    void *a1; size_t a1_stride;
+    void *a2; size_t a2_stride;
+    const void *a3; size_t a3_stride;
+    Scalars *sc;               // per right-hand-side solver state (nullptr: plain operator)
+    int mask;                  // rows to process: 0 all, 1 active, 2 reliable update pending
+    double *partial;           // per-block partial sums
+    unsigned *counter;         // last-block ticket
+    unsigned long long cond;   // cudaGraphConditionalHandle to set (0 = none)
+    int *state;                // solver-wide counters
+};
+
+template <class R> __device__ __forceinline__ const void *rhs_ptr(const void *b, size_t stride, int r) {
+    return reinterpret_cast<const char *>(b) + stride * (size_t)r;
+}
+template <class R> __device__ __forceinline__ void *rhs_ptr(void *b, size_t stride, int r) {
+    return reinterpret_cast<char *>(b) + stride * (size_t)r;
+}
+
+// h = psi_up + s A_mu psi_dn, h[sp*3 + colour], sp = 0, 1
+template <int MU, int S, class R>
+__device__ __forceinline__ void project(const C<R> (&p)[12], C<R> (&h)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<R> d2 = p[6 + c], d3 = p[9 + c];
+        C<R> a0, a1;
+        if (MU == 0) { a0 = cmuli(d3); a1 = cmuli(d2); }
+        else if (MU == 1) { a0 = cneg(d3); a1 = d2; }
+        else if (MU == 2) { a0 = cmuli(d2); a1 = cneg(cmuli(d3)); }
+        else { a0 = d2; a1 = d3; }
+        if (S > 0) { h[c] = cadd(p[c], a0); h[3 + c] = cadd(p[3 + c], a1); }
+        else { h[c] = csub(p[c], a0); h[3 + c] = csub(p[3 + c], a1); }
+    }
+}
+
+// acc_up += w, acc_dn += s A_mu^dag w
+template <int MU, int S, class R>
+__device__ __forceinline__ void accumulate(C<R> (&acc)[12], const C<R> (&w)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<R> w0 = w[c], w1 = w[3 + c];
+        acc[c] = cadd(acc[c], w0);
+        acc[3 + c] = cadd(acc[3 + c], w1);
+        C<R> b0, b1;  // A^dag (w0, w1)
+        if (MU == 0) { b0 = cneg(cmuli(w1)); b1 = cneg(cmuli(w0)); }
+        else if (MU == 1) { b0 = w1; b1 = cneg(w0); }
+        else if (MU == 2) { b0 = cneg(cmuli(w0)); b1 = cmuli(w1); }
+        else { b0 = w0; b1 = w1; }
+        if (S > 0) { acc[6 + c] = cadd(acc[6 + c], b0); acc[9 + c] = cadd(acc[9 + c], b1); }
+        else { acc[6 + c] = csub(acc[6 + c], b0); acc[9 + c] = csub(acc[9 + c], b1); }
+    }
+}
+
+// w = U h (forward) or U^dag h (backward), two colour vectors; optional sign flip
+template <bool ADJ, class R>
+__device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], bool flip) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C<R> s;
+            if (!ADJ) {
+                s = cmul(u[3 * a + 0], h[3 * sp + 0]);
+                s = cadd(s, cmul(u[3 * a + 1], h[3 * sp + 1]));
+                s = cadd(s, cmul(u[3 * a + 2], h[3 * sp + 2]));
+            } else {
+                s = cmulc(u[0 + a], h[3 * sp + 0]);
+                s = cadd(s, cmulc(u[3 + a], h[3 * sp + 1]));
+                s = cadd(s, cmulc(u[6 + a], h[3 * sp + 2]));
+            }
+            w[3 * sp + a] = flip ? cneg(s) : s;
+        }
+}
+
+template <int P, int RECON, bool DAG, int MU>
+__device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const char *gdir, int s, int c,
+                                        C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma
+    const int L = g.L[MU], st = g.stride[MU];
+    {
+        const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+        C<R> p[12], h[6], w[6], u[9];
+        SpinorIO<P>::load(in, g.Vs, sf, p);
+        project<MU, SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
+        su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
+        accumulate<MU, SF>(acc, w);
+    }
+    {
+        const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+        C<R> p[12], h[6], w[6], u[9];
+        SpinorIO<P>::load(in, g.Vs, sb, p);
+        project<MU, -SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
+        su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+        accumulate<MU, -SF>(acc, w);
+    }
+}
+
+// acc = sum over the 8 hops (the bracket of Eq. (1)) at site s of field `in`.
+template <int P, int RECON, bool DAG>
+__device__ __forceinline__ void hopping(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes, int s,
+                                        C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = C<R>{R(0), R(0)};
+    int rem = s;
+    const int x = rem % g.L[0]; rem /= g.L[0];
+    const int y = rem % g.L[1]; rem /= g.L[1];
+    const int z = rem % g.L[2];
+    const int t = rem / g.L[2];
+    const char *gb = reinterpret_cast<const char *>(gauge);
+    hop_dir<P, RECON, DAG, 0>(g, in, gb, s, x, acc);
+    hop_dir<P, RECON, DAG, 1>(g, in, gb + gdir_bytes, s, y, acc);
+    hop_dir<P, RECON, DAG, 2>(g, in, gb + 2 * gdir_bytes, s, z, acc);
+    hop_dir<P, RECON, DAG, 3>(g, in, gb + 3 * gdir_bytes, s, t, acc);
+}
+
+// Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks
+// the site tiles bx, bx + gridDim.x, ... (grid-stride, so the grid can be sized to
+// the machine and reductions have one partial per resident block); thread (x, y)
+// handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
+// one site; Ep::finish runs once per thread after the loop (block and grid
+// reductions, solver scalars).
+template <int P, int RECON, bool DAG, class Ep>
+__global__ void __launch_bounds__(256) dslash_kernel(DslashArgs a) {
+    using R = typename Real<P>::T;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool row = r < a.nrhs && row_on(a.sc, a.mask, r);
+    const void *in = rhs_ptr<R>(a.in, a.in_stride, r < a.nrhs ? r : 0);
+    typename Ep::State st{};
+    for (int s0 = blockIdx.x * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        if (row && s < a.g.V) {
+            C<R> acc[12];
+            hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            Ep::template site<P>(a, s, r, in, acc, st);
+        }
+    }
+    Ep::template finish<P>(a, r, row, st);
+}
+
+// ---------------------------------------------------------------- epilogues
+// out = in - kappa * hop     (D or D^dag applied to in)
+struct EpXpay {
+    struct State {};
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
+                                                State &) {
+        C<R> p[12];
+        SpinorIO<P>::load(in, a.g.Vs, s, p);
+        const R k = R(a.kappa);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
+        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &, int, bool, State &) {}
+};
+
+template <class R, int N> __device__ __forceinline__ double norm2_of(const C<R> (&v)[N]) {
+    double n = 0.0;
+#pragma unroll
+    for (int c = 0; c < N; ++c) n += (double)v[c].re * (double)v[c].re + (double)v[c].im * (double)v[c].im;
+    return n;
+}
+
+}  // namespace wd

@@ -1,0 +1,30 @@
+// Plain Dslash launches: out = D in or out = D^dag in, every precision and link
+// compression (section 2.1, Eq. (1); section 2.2, gamma5-hermiticity).
+#include "dslash.cuh"
+#include "wd_host.h"
+
+namespace wd {
+
+template <int P, int RECON, bool DAG>
+static cudaError_t go(const DslashArgs &a, DslashTiles t, cudaStream_t st) {
+    dim3 block(t.site_tile, t.rhs_tile);
+    dim3 grid((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    dslash_kernel<P, RECON, DAG, EpXpay><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t go_p(const DslashArgs &a, int recon, bool dagger, DslashTiles t, cudaStream_t st) {
+    if (recon == 12) return dagger ? go<P, 12, true>(a, t, st) : go<P, 12, false>(a, t, st);
+    return dagger ? go<P, 18, true>(a, t, st) : go<P, 18, false>(a, t, st);
+}
+
+cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, DslashTiles t, cudaStream_t st) {
+    switch (p) {
+    case F64: return go_p<F64>(a, recon, dagger, t, st);
+    case F32: return go_p<F32>(a, recon, dagger, t, st);
+    default: return go_p<F16>(a, recon, dagger, t, st);
+    }
+}
+
+}  // namespace wd

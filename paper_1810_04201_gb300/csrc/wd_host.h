@@ -1,0 +1,41 @@
+// Host-side internal interface shared by the translation units of libwd.
+#pragma once
+#include <cstdio>
+#include <string>
+#include "wd_internal.cuh"
+
+namespace wd {
+
+struct DslashArgs;
+struct VecArgs;
+
+// status helpers
+wd_status fail(wd_ctx *c, wd_status s, const std::string &msg);
+wd_status cuda_fail(wd_ctx *c, cudaError_t e, const char *where);
+#define WD_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::wd::cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// workspace: named device buffer of at least `bytes` (kept across calls)
+wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);
+// device gauge field of precision p at the context's recon (created on first use)
+wd_status gauge_get(wd_ctx *c, Prec p, const void **out);
+size_t gauge_dir_bytes(const wd_ctx *c, Prec p);
+
+DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs);
+
+// Launchers of the plain operators (xpay epilogue): out = in - kappa * hop
+// (dagger = 0: D, dagger = 1: D^dag).  Used by wd_apply and the autotuner.
+cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, DslashTiles t, cudaStream_t st);
+
+// Kernel-node description for graph building and direct launches.
+struct KernelCall {
+    const void *func;
+    dim3 grid, block;
+    size_t smem;
+    void *args[1];  // every kernel of the library takes one struct argument
+};
+
+}  // namespace wd

@@ -1,0 +1,342 @@
+// Internal types, field layouts and device helpers of libwd (sm_103a).
+//
+// Field layouts are described in include/wd.h.  Gauge layouts (per direction mu,
+// blocks of Vs sites, complex entries row-major A*3+B):
+//   F64 recon-18: 9 arrays of Vs double2            recon-12: 6 arrays (rows 0, 1)
+//   F32 recon-18: 4 arrays of Vs float4 (entries 0-7) + 1 array of Vs float2 (entry 8)
+//   F32 recon-12: 3 arrays of Vs float4
+//   F16 recon-18: 2 arrays of Vs uint4 (8 half2 entries 0-7) + 1 array of Vs half2
+//   F16 recon-12: 1 array of Vs uint4 (entries 0-3) + 1 array of Vs uint2 (entries 4-5)
+// Link entries have modulus <= 1 (unitary matrices), so FP16 links need no scale.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/wd.h"
+
+namespace wd {
+
+enum Prec { F64 = 0, F32 = 1, F16 = 2 };
+
+constexpr int kSiteAlign = 64;
+inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// ------------------------------------------------------------------ complex
+template <class R> struct C { R re, im; };
+
+template <class R> __device__ __forceinline__ C<R> cmk(R a, R b) { return C<R>{a, b}; }
+template <class R> __device__ __forceinline__ C<R> cadd(C<R> a, C<R> b) { return C<R>{a.re + b.re, a.im + b.im}; }
+template <class R> __device__ __forceinline__ C<R> csub(C<R> a, C<R> b) { return C<R>{a.re - b.re, a.im - b.im}; }
+template <class R> __device__ __forceinline__ C<R> cneg(C<R> a) { return C<R>{-a.re, -a.im}; }
+template <class R> __device__ __forceinline__ C<R> cconj(C<R> a) { return C<R>{a.re, -a.im}; }
+// i * a
+template <class R> __device__ __forceinline__ C<R> cmuli(C<R> a) { return C<R>{-a.im, a.re}; }
+template <class R> __device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
+    return C<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <class R> __device__ __forceinline__ C<R> cmulc(C<R> a, C<R> b) {
+    return C<R>{a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <class R> __device__ __forceinline__ C<R> cscale(R s, C<R> a) { return C<R>{s * a.re, s * a.im}; }
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+    int L[4];
+    int V;
+    int Vs;          // site stride of field arrays (V rounded up to kSiteAlign)
+    int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int antiperiodic;
+};
+
+// ------------------------------------------------------------------ field sizes
+inline size_t spinor_bytes(Prec p, int Vs) {
+    switch (p) {
+    case F64: return (size_t)12 * Vs * 16;
+    case F32: return (size_t)6 * Vs * 16;
+    default: return round_up((size_t)3 * Vs * 16 + (size_t)Vs * 4, 256);
+    }
+}
+inline size_t link_dir_bytes(Prec p, int recon, int Vs) {
+    if (p == F64) return (size_t)(recon == 12 ? 6 : 9) * Vs * 16;
+    if (p == F32) return recon == 12 ? (size_t)3 * Vs * 16 : (size_t)4 * Vs * 16 + (size_t)Vs * 8;
+    return recon == 12 ? (size_t)Vs * 16 + (size_t)Vs * 8 : (size_t)2 * Vs * 16 + (size_t)Vs * 4;
+}
+inline size_t gauge_bytes(Prec p, int recon, int Vs) { return 4 * round_up(link_dir_bytes(p, recon, Vs), 256); }
+
+// ------------------------------------------------------------------ precision traits
+template <int P> struct Real { using T = float; };
+template <> struct Real<F64> { using T = double; };
+
+// Spinor load/store: v[spin*3 + colour]
+template <int P> struct SpinorIO;
+
+template <> struct SpinorIO<F64> {
+    using R = double;
+    static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
+        const double2 *p = reinterpret_cast<const double2 *>(base) + s;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 t = __ldg(p + (size_t)c * Vs);
+            v[c] = C<R>{t.x, t.y};
+        }
+    }
+    static __device__ __forceinline__ void store(void *base, int Vs, int s, const C<R> (&v)[12]) {
+        double2 *p = reinterpret_cast<double2 *>(base) + s;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[(size_t)c * Vs] = make_double2(v[c].re, v[c].im);
+    }
+};
+
+template <> struct SpinorIO<F32> {
+    using R = float;
+    static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
+        const float4 *p = reinterpret_cast<const float4 *>(base) + s;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            float4 t = __ldg(p + (size_t)j * Vs);
+            v[2 * j] = C<R>{t.x, t.y};
+            v[2 * j + 1] = C<R>{t.z, t.w};
+        }
+    }
+    static __device__ __forceinline__ void store(void *base, int Vs, int s, const C<R> (&v)[12]) {
+        float4 *p = reinterpret_cast<float4 *>(base) + s;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) p[(size_t)j * Vs] = make_float4(v[2 * j].re, v[2 * j].im, v[2 * j + 1].re, v[2 * j + 1].im);
+    }
+};
+
+__device__ __forceinline__ float2 h2f(uint32_t u) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <> struct SpinorIO<F16> {
+    using R = float;
+    static __device__ __forceinline__ const float *norms(const void *base, int Vs) {
+        return reinterpret_cast<const float *>(reinterpret_cast<const char *>(base) + (size_t)3 * Vs * 16);
+    }
+    static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(base) + s;
+        const float nrm = __ldg(norms(base, Vs) + s);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 t = __ldg(p + (size_t)j * Vs);
+            float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+            v[4 * j + 0] = C<R>{a.x * nrm, a.y * nrm};
+            v[4 * j + 1] = C<R>{b.x * nrm, b.y * nrm};
+            v[4 * j + 2] = C<R>{c.x * nrm, c.y * nrm};
+            v[4 * j + 3] = C<R>{d.x * nrm, d.y * nrm};
+        }
+    }
+    static __device__ __forceinline__ void store(void *base, int Vs, int s, const C<R> (&v)[12]) {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf(v[c].re), fabsf(v[c].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4 *p = reinterpret_cast<uint4 *>(base) + s;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 t;
+            t.x = f2h(v[4 * j + 0].re * inv, v[4 * j + 0].im * inv);
+            t.y = f2h(v[4 * j + 1].re * inv, v[4 * j + 1].im * inv);
+            t.z = f2h(v[4 * j + 2].re * inv, v[4 * j + 2].im * inv);
+            t.w = f2h(v[4 * j + 3].re * inv, v[4 * j + 3].im * inv);
+            p[(size_t)j * Vs] = t;
+        }
+        float *nrm = const_cast<float *>(norms(base, Vs));
+        nrm[s] = m;
+    }
+};
+
+// Link load: u[A*3+B] of U_mu(s); recon-12 rebuilds row 2 = conj(row0 x row1).
+template <class R> __device__ __forceinline__ void rebuild_row2(C<R> (&u)[9]) {
+    u[6] = cconj(csub(cmul(u[1], u[5]), cmul(u[2], u[4])));
+    u[7] = cconj(csub(cmul(u[2], u[3]), cmul(u[0], u[5])));
+    u[8] = cconj(csub(cmul(u[0], u[4]), cmul(u[1], u[3])));
+}
+
+template <int P, int RECON> struct LinkIO;
+
+template <int RECON> struct LinkIO<F64, RECON> {
+    using R = double;
+    static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
+        const double2 *p = reinterpret_cast<const double2 *>(dir_base) + s;
+        constexpr int n = RECON == 12 ? 6 : 9;
+#pragma unroll
+        for (int e = 0; e < n; ++e) {
+            double2 t = __ldg(p + (size_t)e * Vs);
+            u[e] = C<R>{t.x, t.y};
+        }
+        if (RECON == 12) rebuild_row2(u);
+    }
+};
+
+template <int RECON> struct LinkIO<F32, RECON> {
+    using R = float;
+    static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
+        const float4 *p = reinterpret_cast<const float4 *>(dir_base) + s;
+        constexpr int n4 = RECON == 12 ? 3 : 4;
+#pragma unroll
+        for (int j = 0; j < n4; ++j) {
+            float4 t = __ldg(p + (size_t)j * Vs);
+            u[2 * j] = C<R>{t.x, t.y};
+            u[2 * j + 1] = C<R>{t.z, t.w};
+        }
+        if (RECON == 12) {
+            rebuild_row2(u);
+        } else {
+            const float2 *q = reinterpret_cast<const float2 *>(reinterpret_cast<const float4 *>(dir_base) + (size_t)4 * Vs) + s;
+            float2 t = __ldg(q);
+            u[8] = C<R>{t.x, t.y};
+        }
+    }
+};
+
+template <int RECON> struct LinkIO<F16, RECON> {
+    using R = float;
+    static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(dir_base) + s;
+        if (RECON == 12) {
+            uint4 t = __ldg(p);
+            float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+            u[0] = C<R>{a.x, a.y}; u[1] = C<R>{b.x, b.y}; u[2] = C<R>{c.x, c.y}; u[3] = C<R>{d.x, d.y};
+            const uint2 *q = reinterpret_cast<const uint2 *>(reinterpret_cast<const uint4 *>(dir_base) + Vs) + s;
+            uint2 w = __ldg(q);
+            float2 e = h2f(w.x), f = h2f(w.y);
+            u[4] = C<R>{e.x, e.y}; u[5] = C<R>{f.x, f.y};
+            rebuild_row2(u);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uint4 t = __ldg(p + (size_t)j * Vs);
+                float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+                u[4 * j + 0] = C<R>{a.x, a.y}; u[4 * j + 1] = C<R>{b.x, b.y};
+                u[4 * j + 2] = C<R>{c.x, c.y}; u[4 * j + 3] = C<R>{d.x, d.y};
+            }
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint4 *>(dir_base) + (size_t)2 * Vs) + s;
+            float2 t = h2f(__ldg(q));
+            u[8] = C<R>{t.x, t.y};
+        }
+    }
+};
+
+// ------------------------------------------------------------------ reductions
+// Deterministic block reduction of NV doubles per row of a (SB x RT) block.  SB is a
+// power of two (16 .. 256) and SB * RT a multiple of 32, so the shuffle groups of
+// min(SB, 32) lanes never straddle two rows.  Result valid in threadIdx.x == 0.
+// smem: at least RT * 8 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_reduce_rows(double (&v)[NV], double *smem) {
+    const int SB = blockDim.x;
+    const int width = SB < 32 ? SB : 32;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = width >> 1; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (SB + 31) >> 5;
+    double *row = smem + (size_t)threadIdx.y * 8 * NV;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) row[w * NV + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < nw; ++i) s += row[i * NV + k];
+            v[k] = s;
+        }
+    }
+}
+
+// Last-block-done grid reduction.  Each block has written its per-row partials to
+// partial[(rhs * NV + k) * nblk + blockIdx.x]; the block that finishes last sums
+// them in block order (deterministic) and returns true in every thread of that
+// block, with the totals in tot[rhs*NV + k] (shared memory, visible after the call).
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        unsigned t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double *partial, int nblk, int nrows, double *tot) {
+    // one warp per (row, k); lanes stride over blocks, then a fixed-order tree
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    for (int q = warp; q < nrows * NV; q += nwarp) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += __ldcg(partial + (size_t)q * nblk + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) tot[q] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ solver scalars
+// One record per right-hand side, resident in device memory.
+struct Scalars {
+    double rho;        // |r|^2 of the current residual
+    double rho_new;
+    double pAp;        // |D p|^2
+    double alpha, beta;
+    double rhs2;       // |D^dag b|^2
+    double tol2;       // tol^2 * |D^dag b|^2
+    double rmax2;      // max |r|^2 since the last reliable update
+    double delta2;
+    double true_n2;    // |D^dag (b - D x)|^2 at the end
+    double true_b2;    // |b - D x|^2 at the end
+    double b2;         // |b|^2
+    int iter, max_iter;
+    int active;        // still iterating
+    int status;
+    int reliable;      // number of reliable updates
+    int do_update;     // reliable update requested for this iteration
+    int pad[2];
+};
+
+__device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
+    if (mask == 0 || sc == nullptr) return true;
+    return mask == 1 ? sc[r].active != 0 : sc[r].do_update != 0;
+}
+
+struct DslashTiles { int site_tile = 128; int rhs_tile = 1; };
+
+}  // namespace wd
+
+// The context (opaque in the C ABI).
+struct wd_ctx {
+    wd::Geom g;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int recon = 18;
+    bool has_gauge = false;
+    void *gauge[3] = {nullptr, nullptr, nullptr};    // per precision (at this->recon)
+    double *gauge_canon = nullptr;                     // FP64 canonical copy on device
+    std::string last_error;
+    long long launches = 0;
+    // workspace
+    std::map<std::string, void *> ws;                  // named device buffers
+    std::map<std::string, size_t> ws_size;
+    std::map<std::string, void *> graphs;              // cached cudaGraphExec_t per solver signature
+    std::map<std::string, std::vector<long long>> graph_info;
+    std::map<int, wd::DslashTiles> tiles;              // key: prec*64 + nrhs
+    ~wd_ctx();
+};

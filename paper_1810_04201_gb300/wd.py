@@ -1,0 +1,245 @@
+"""ctypes binding of libwd (include/wd.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+converts Python arguments into C arguments, uses torch for device memory and
+for the current CUDA stream, and turns status codes into exceptions.  There is
+no CPU fallback: importing the binding loads ``_build/libwd.so`` and raises if
+it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libwd.so")
+
+WD_F64, WD_F32, WD_F16 = 0, 1, 2
+PRECS = {"f64": WD_F64, "f32": WD_F32, "f16": WD_F16}
+STATUS = {0: "WD_OK", 1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_OOM", 4: "WD_ERR_NOT_CONVERGED",
+          5: "WD_ERR_BREAKDOWN", 6: "WD_ERR_NONFINITE", 7: "WD_ERR_TIMEOUT", 8: "WD_ERR_STATE"}
+MAX_RHS = 16
+
+
+class CGParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("block", ctypes.c_int),
+                ("rhs_tile", ctypes.c_int)]
+
+
+class CGResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("true_rel_resid_b", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class WDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libwd.so and declare the C signatures (raises if the library is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libwd.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sigs = {
+        "wd_create": ([ctypes.POINTER(P), ctypes.POINTER(I), I, P], I),
+        "wd_destroy": ([P], I),
+        "wd_set_stream": ([P, P], I),
+        "wd_set_gauge": ([P, P, I, I], I),
+        "wd_field_bytes": ([P, I, I], S),
+        "wd_pack": ([P, P, I, P, I, I], I),
+        "wd_unpack": ([P, P, I, I, P, I], I),
+        "wd_apply": ([P, D, P, P, I, I], I),
+        "wd_apply_dagger": ([P, D, P, P, I, I], I),
+        "wd_normal_apply": ([P, D, P, P, I, I], I),
+        "wd_cg_solve": ([P, D, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
+        "wd_cg_solve_canonical": ([P, D, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
+        "wd_cg_solve_batched": ([PP, ctypes.POINTER(D), PP, PP, I, ctypes.POINTER(CGParams),
+                                 ctypes.POINTER(CGResult)], I),
+        "wd_autotune": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "wd_set_tiles": ([P, I, I, I, I], I),
+        "wd_kernel_launches": ([P], ctypes.c_longlong),
+        "wd_status_string": ([I], ctypes.c_char_p),
+        "wd_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Lattice:
+    """One lattice (dims, boundary, gauge field) bound to a library context.
+
+    Fields are torch uint8 device tensors of ``field_bytes(prec, nrhs)`` bytes in the
+    library's layout; canonical spinors are complex128 arrays (nrhs, V, 4, 3) and
+    canonical links complex128 (4, V, 3, 3).
+    """
+
+    def __init__(self, dims, antiperiodic_t=True, stream=None):
+        self.lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.ctx = ctypes.c_void_p()
+        d = (ctypes.c_int * 4)(*self.dims)
+        st = self.lib.wd_create(ctypes.byref(self.ctx), d, int(bool(antiperiodic_t)), _stream_ptr(stream))
+        if st != 0:
+            raise WDError(st, "wd_create failed")
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.wd_last_error(self.ctx).decode()
+            raise WDError(st, f"{what}: {msg}")
+
+    def close(self):
+        if self.ctx:
+            self.lib.wd_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        self._check(self.lib.wd_set_stream(self.ctx, _stream_ptr(stream)), "wd_set_stream")
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.wd_kernel_launches(self.ctx))
+
+    def field_bytes(self, prec=WD_F64, nrhs=1) -> int:
+        return int(self.lib.wd_field_bytes(self.ctx, prec, nrhs))
+
+    def new_field(self, prec=WD_F64, nrhs=1, zero=True):
+        n = self.field_bytes(prec, nrhs)
+        return torch.zeros(n, dtype=torch.uint8, device="cuda") if zero else \
+            torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    # ------------------------------------------------------------------ gauge / layout
+    def set_gauge(self, U, recon=18):
+        """U: canonical links, numpy complex128 (4, V, 3, 3) or a complex128 cuda tensor."""
+        if isinstance(U, torch.Tensor) and U.is_cuda:
+            t = U.contiguous()
+            self._check(self.lib.wd_set_gauge(self.ctx, ctypes.c_void_p(t.data_ptr()), 1, recon), "wd_set_gauge")
+            torch.cuda.current_stream().synchronize()
+        else:
+            a = np.ascontiguousarray(U, dtype=np.complex128)
+            assert a.shape == (4, self.V, 3, 3)
+            self._check(self.lib.wd_set_gauge(self.ctx, a.ctypes.data_as(ctypes.c_void_p), 0, recon),
+                        "wd_set_gauge")
+
+    def pack(self, psi, prec=WD_F64, out=None):
+        """Canonical spinor(s) (numpy or cuda complex128, (V,4,3) or (nrhs,V,4,3)) -> field."""
+        nrhs = 1 if (psi.ndim == 3) else psi.shape[0]
+        if out is None:
+            out = self.new_field(prec, nrhs, zero=False)
+        if isinstance(psi, torch.Tensor) and psi.is_cuda:
+            t = psi.contiguous()
+            st = self.lib.wd_pack(self.ctx, ctypes.c_void_p(t.data_ptr()), 1, ctypes.c_void_p(out.data_ptr()), prec,
+                                  nrhs)
+        else:
+            a = np.ascontiguousarray(psi, dtype=np.complex128)
+            st = self.lib.wd_pack(self.ctx, a.ctypes.data_as(ctypes.c_void_p), 0, ctypes.c_void_p(out.data_ptr()),
+                                  prec, nrhs)
+        self._check(st, "wd_pack")
+        return out
+
+    def unpack(self, field, prec=WD_F64, nrhs=1, squeeze=True):
+        """Field -> canonical numpy complex128 (nrhs, V, 4, 3) (squeezed for nrhs = 1)."""
+        out = np.empty((nrhs, self.V, 4, 3), dtype=np.complex128)
+        self._check(self.lib.wd_unpack(self.ctx, ctypes.c_void_p(field.data_ptr()), prec, nrhs,
+                                       out.ctypes.data_as(ctypes.c_void_p), 0), "wd_unpack")
+        return out[0] if (squeeze and nrhs == 1) else out
+
+    # ------------------------------------------------------------------ operators
+    def apply(self, kappa, src, dst, prec=WD_F64, nrhs=1, dagger=False):
+        fn = self.lib.wd_apply_dagger if dagger else self.lib.wd_apply
+        self._check(fn(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                       prec, nrhs), "wd_apply_dagger" if dagger else "wd_apply")
+        return dst
+
+    def normal_apply(self, kappa, src, dst, prec=WD_F64, nrhs=1):
+        self._check(self.lib.wd_normal_apply(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
+                                             ctypes.c_void_p(dst.data_ptr()), prec, nrhs), "wd_normal_apply")
+        return dst
+
+    # ------------------------------------------------------------------ solvers
+    @staticmethod
+    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1, block=0, rhs_tile=0):
+        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile)
+
+    def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1, block=0,
+           raise_on_fail=True):
+        """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results."""
+        p = self.params(tol, max_iter, inner, delta, nrhs, block)
+        res = (CGResult * nrhs)()
+        st = self.lib.wd_cg_solve(self.ctx, float(kappa), ctypes.c_void_p(b.data_ptr()),
+                                  ctypes.c_void_p(x.data_ptr()), ctypes.byref(p), res)
+        if raise_on_fail:
+            self._check(st, "wd_cg_solve")
+        return [r.as_dict() for r in res], st
+
+    def cg_canonical(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1,
+                     raise_on_fail=True):
+        """End-to-end solve on canonical host arrays (numpy complex128, pinned torch CPU tensors
+        allowed) or device tensors; x is overwritten with the solution."""
+        p = self.params(tol, max_iter, inner, delta, nrhs, 0)
+        res = (CGResult * nrhs)()
+        if isinstance(b, torch.Tensor):
+            on_dev = int(b.is_cuda)
+            bp, xp = ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr())
+        else:
+            on_dev = 0
+            bp, xp = b.ctypes.data_as(ctypes.c_void_p), x.ctypes.data_as(ctypes.c_void_p)
+        st = self.lib.wd_cg_solve_canonical(self.ctx, float(kappa), bp, xp, on_dev, ctypes.byref(p), res)
+        if raise_on_fail:
+            self._check(st, "wd_cg_solve_canonical")
+        return [r.as_dict() for r in res], st
+
+    def autotune(self, prec=WD_F64, nrhs=1):
+        st_, rt = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wd_autotune(self.ctx, prec, nrhs, ctypes.byref(st_), ctypes.byref(rt)), "wd_autotune")
+        return st_.value, rt.value
+
+    def set_tiles(self, prec, nrhs, site_tile, rhs_tile):
+        self._check(self.lib.wd_set_tiles(self.ctx, prec, nrhs, site_tile, rhs_tile), "wd_set_tiles")
+
+
+def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32, delta=0.1):
+    """Solve many independent lattices in one persistent launch (wd_cg_solve_batched)."""
+    lib = load_library()
+    n = len(lattices)
+    ctxs = (ctypes.c_void_p * n)(*[L.ctx.value for L in lattices])
+    ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0)
+    res = (CGResult * n)()
+    st = lib.wd_cg_solve_batched(ctxs, ks, bp, xp, n, ctypes.byref(p), res)
+    return [r.as_dict() for r in res], st

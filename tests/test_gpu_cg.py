@@ -1,0 +1,143 @@
+"""GPU CG solvers against the CPU oracle (through the C ABI).
+
+Bar: true FP64 normal residual <= 1e-10 recomputed by the library, and the
+solution within 1e-9 (relative 2-norm) of the oracle solution iterated to
+1e-13, on lattices whose condition number keeps that bound (Haar links,
+kappa <= 0.125: cond(D) about 4).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_04201_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_04201_gb300 import wd as _wd
+    return _wd
+
+
+def ref_solution(U, b, kappa, dims):
+    x, info = oracle.cgnr(U, b, kappa, dims, tol=1e-13, max_iter=20000)
+    assert info["converged"]
+    return x, info
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+def test_cg_4x4(wd, inner):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=1)
+    b = gen.gaussian_source(dims, seed=1)
+    x_ref, info = ref_solution(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(b), lat.new_field()
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner)
+    r = res[0]
+    assert st == 0 and r["status"] == 0
+    assert r["true_rel_resid"] <= 1e-10
+    assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+    if inner == 0:
+        _, i10 = oracle.cgnr(U, b, kappa, dims, tol=1e-10)
+        assert abs(r["iters"] - i10["iters"]) <= 1
+    else:
+        assert r["reliable_updates"] >= 1
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_cg_odd_shapes(wd, inner, recon):
+    dims, kappa = (6, 6, 6, 8), 0.124
+    U = gen.haar_links(dims, seed=3)
+    b = gen.gaussian_source(dims, seed=4)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=recon)
+    fb, fx = lat.pack(b), lat.new_field()
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner)
+    assert st == 0 and res[0]["true_rel_resid"] <= 1e-10
+    assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+
+
+def test_cg_dense_lu_2x4(wd):
+    """On 2^4 (each neighbour reached twice) the solution matches LAPACK's LU solve."""
+    dims, kappa = (2, 2, 2, 2), 0.12
+    U = gen.haar_links(dims, seed=21)
+    b = gen.gaussian_source(dims, seed=22)
+    xd = oracle.dense_solve(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(b), lat.new_field()
+    res, st = lat.cg(kappa, fb, fx, tol=1e-12)
+    assert st == 0
+    assert oracle.rel_err(lat.unpack(fx), xd) < 1e-10
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_cg_multi_rhs_point_sources(wd, inner):
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = gen.haar_links(dims, seed=7)
+    B = gen.propagator_sources(dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(B), lat.new_field(nrhs=12)
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner, nrhs=12)
+    assert st == 0
+    X = lat.unpack(fx, nrhs=12)
+    for k in (0, 5, 11):
+        x_ref, _ = ref_solution(U, B[k], kappa, dims)
+        assert oracle.rel_err(X[k], x_ref) < 1e-9
+    assert all(r["true_rel_resid"] <= 1e-10 for r in res)
+
+
+def test_cg_initial_guess_and_zero_source(wd):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=1)
+    b = gen.gaussian_source(dims, seed=2)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(b), lat.new_field()
+    r1, _ = lat.cg(kappa, fb, fx, tol=1e-10)
+    r2, st = lat.cg(kappa, fb, fx, tol=1e-10)  # resume from the converged solution
+    assert st == 0 and r2[0]["iters"] == 0
+    z = lat.pack(np.zeros_like(b))
+    fz = lat.new_field()
+    r3, st = lat.cg(kappa, z, fz, tol=1e-10)
+    assert st == 0 and r3[0]["iters"] == 0
+    assert not lat.unpack(fz).any()
+
+
+def test_cg_failure_statuses(wd):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=1)
+    b = gen.gaussian_source(dims, seed=2)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(b), lat.new_field()
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, max_iter=3, raise_on_fail=False)
+    assert st == 4 and res[0]["iters"] == 3
+    bn = b.copy()
+    bn[5, 1, 2] = np.nan
+    res, st = lat.cg(kappa, lat.pack(bn), lat.new_field(), tol=1e-10, raise_on_fail=False)
+    assert st == 6
+    res, st = lat.cg(kappa, lat.pack(bn), lat.new_field(), tol=1e-10, inner=1, raise_on_fail=False)
+    assert st == 6
+
+
+def test_cg_canonical_host_buffers(wd):
+    import torch
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=1)
+    b = gen.gaussian_source(dims, seed=1)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    bt = torch.from_numpy(b.copy()).pin_memory()
+    xt = torch.zeros_like(bt).pin_memory()
+    res, st = lat.cg_canonical(kappa, bt, xt, tol=1e-10)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    assert st == 0 and oracle.rel_err(xt.numpy(), x_ref) < 1e-9

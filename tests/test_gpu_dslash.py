@@ -1,0 +1,137 @@
+"""GPU parity of the Dslash kernels against the CPU oracle (through the C ABI).
+
+Tolerances (relative per-field 2-norm):
+  * FP64: 1e-13 (the operator is exact up to rounding; FMA contraction and the
+    half-spinor form change the rounding order only, ~1e-16 per site);
+  * FP32: 2e-6 (single-precision storage of inputs and links, about 40 rounding
+    steps per output component at 6e-8 each);
+  * FP16 storage: 4e-3 (half-precision storage, 2^-11 relative to the per-site
+    scale, FP32 arithmetic).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_04201_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3}
+KAPPA = 0.12
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_04201_gb300 import wd as _wd
+    return _wd
+
+
+SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 6, 6, 8), (3, 5, 4, 6), (8, 8, 8, 12), (4, 6, 8, 10)]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_dslash_parity(wd, dims, prec, recon):
+    U = gen.haar_links(dims, seed=2)
+    psi = gen.gaussian_source(dims, seed=3)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=recon)
+    f = lat.pack(psi, prec)
+    for dagger in (False, True):
+        o = lat.new_field(prec)
+        lat.apply(KAPPA, f, o, prec, dagger=dagger)
+        got = lat.unpack(o, prec)
+        ref = oracle.apply_D(U, psi, KAPPA, dims, dagger=dagger)
+        assert oracle.rel_err(got, ref) < TOL[prec], (dagger, oracle.rel_err(got, ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_periodic_time_and_paper_sign(wd, prec):
+    dims = (4, 4, 2, 6)
+    U = gen.haar_links(dims, seed=8)
+    psi = gen.gaussian_source(dims, seed=9)
+    lat = wd.Lattice(dims, antiperiodic_t=False)
+    lat.set_gauge(U)
+    f = lat.pack(psi, prec)
+    o = lat.new_field(prec)
+    lat.apply(-KAPPA, f, o, prec)  # the paper's +kappa convention
+    ref = oracle.apply_D(U, psi, -KAPPA, dims, antiperiodic_t=False)
+    assert oracle.rel_err(lat.unpack(o, prec), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("nrhs,tiles", [(3, (64, 1)), (5, (32, 4)), (12, (16, 12)), (12, (32, 8)), (7, (128, 2))])
+def test_multi_rhs_parity(wd, nrhs, tiles):
+    dims = (4, 4, 6, 4)
+    U = gen.haar_links(dims, seed=4)
+    psi = gen.gaussian_source(dims, seed=5, nrhs=nrhs)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    for prec in (0, 1):
+        lat.set_tiles(prec, nrhs, *tiles)
+        f = lat.pack(psi, prec)
+        o = lat.new_field(prec, nrhs)
+        lat.apply(KAPPA, f, o, prec, nrhs=nrhs)
+        got = lat.unpack(o, prec, nrhs)
+        for r in range(nrhs):
+            assert oracle.rel_err(got[r], oracle.apply_D(U, psi[r], KAPPA, dims)) < TOL[prec]
+
+
+def test_normal_op_parity(wd):
+    dims = (4, 4, 4, 8)
+    U = gen.haar_links(dims, seed=6)
+    psi = gen.gaussian_source(dims, seed=7)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    f = lat.pack(psi)
+    o = lat.new_field()
+    lat.normal_apply(KAPPA, f, o)
+    assert oracle.rel_err(lat.unpack(o), oracle.apply_normal(U, psi, KAPPA, dims)) < 1e-13
+
+
+def test_pack_unpack_roundtrip_bit_exact(wd):
+    dims = (3, 5, 4, 6)
+    psi = gen.gaussian_source(dims, seed=1, nrhs=2)
+    lat = wd.Lattice(dims)
+    f = lat.pack(psi, 0)
+    np.testing.assert_array_equal(lat.unpack(f, 0, 2), psi)
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16, 16), (32, 32, 32, 64)])
+def test_full_size_sampled(wd, dims):
+    """Full-size lattices: GPU output compared with the oracle at sampled sites."""
+    U = gen.haar_links(dims, seed=10) if dims[3] == 16 else gen.smoothed_links(dims, seed=6, eps=0.4)
+    psi = gen.gaussian_source(dims, seed=11)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    V = int(np.prod(dims))
+    sites = np.unique(np.concatenate([np.arange(64), V - 1 - np.arange(64),
+                                      gen.uniform(3, 9, 0, 256).__mul__(V).astype(np.int64)]))
+    for prec in (0, 1):
+        f = lat.pack(psi, prec)
+        o = lat.new_field(prec)
+        for dagger in (False, True):
+            lat.apply(KAPPA, f, o, prec, dagger=dagger)
+            got = lat.unpack(o, prec)[sites]
+            ref = oracle.apply_D_sites(U, psi, KAPPA, dims, sites, dagger=dagger)
+            assert oracle.rel_err(got, ref) < TOL[prec]
+
+
+def test_argument_errors(wd):
+    lat = wd.Lattice((4, 4, 4, 4))
+    f = lat.new_field()
+    with pytest.raises(wd.WDError) as e:
+        lat.apply(KAPPA, f, lat.new_field())
+    assert e.value.status == 8  # no gauge yet
+    lat.set_gauge(gen.unit_links((4, 4, 4, 4)))
+    with pytest.raises(wd.WDError) as e:
+        lat.apply(KAPPA, f, f)
+    assert e.value.status == 1
+    with pytest.raises(wd.WDError):
+        lat.apply(KAPPA, f, lat.new_field(), nrhs=17)
+    with pytest.raises(wd.WDError):
+        lat.set_tiles(0, 4, 48, 1)
+    with pytest.raises(wd.WDError):
+        wd.Lattice((4, 1, 4, 4))
