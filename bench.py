@@ -232,8 +232,14 @@ def main():
     ap.add_argument("--recon", type=int, default=18, choices=[18, 12])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="also time the Dslash at 8^4, 12^4, 16^4, 24^4")
+    ap.add_argument("--dslash-only", default=None, metavar="LX,LY,LZ,LT",
+                    help="time only the Dslash kernel on this lattice (profiling helper)")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
+    ap.add_argument("--nrhs", type=int, default=1)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.dslash_only:
+        return dslash_only(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -398,6 +404,41 @@ def main():
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def dslash_only(args):
+    """W warm-up and K timed launches of one Dslash (D, xpay) on a Haar lattice."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_04201_gb300 import gen, wd
+    dims = tuple(int(x) for x in args.dslash_only.split(","))
+    lat = wd.Lattice(dims)
+    lat.set_gauge(gen.haar_links(dims, 3), recon=args.recon)
+    b = gen.gaussian_source(dims, 4, nrhs=args.nrhs)
+    pid = PREC_ID[args.prec]
+    fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
+    fo = lat.new_field(pid, args.nrhs)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        lat.apply(0.12, fi, fo, pid, args.nrhs)
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.apply(0.12, fi, fo, pid, args.nrhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.mean(ts)
+    V = lat.V
+    nb = V * (args.nrhs * 2 * SPINOR_BYTES[args.prec] + LINK_BYTES[(args.prec, args.recon)])
+    print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs,
+                      "ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V * args.nrhs / ms / 1e6, 1),
+                      "algorithmic_gbs": round(nb / ms / 1e6, 1), "bytes_per_launch": nb}))
 
 
 def sweep(wd, torch, flush, stream, recon):
