@@ -107,6 +107,28 @@ wd_status wd_apply_dagger(wd_ctx *ctx, double kappa, const void *in, void *out, 
  * context-owned temporary field. */
 wd_status wd_normal_apply(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
 
+/* out = D^dag D in, like wd_normal_apply, but without allocating device memory.
+ *
+ * For callers that cannot call cudaMalloc: a process whose device-memory budget is
+ * fixed once at start-up (a memory pool that owns the rest of the GPU), or a
+ * latency-critical loop that must not pay for cudaMalloc/cudaFree, which may
+ * synchronise the whole device.  The paper has no counterpart; this is an
+ * interface variant of wd_normal_apply.
+ *
+ * The intermediate field D in lives in a fixed file-scope device array of
+ * 16 MiB (every GPU that loads the library keeps it until the process exits), so
+ * wd_field_bytes(ctx, prec, nrhs) must not exceed 16 MiB: larger requests return
+ * WD_ERR_ARG before anything is launched (FP64 fits 16^4 sites with one
+ * right-hand side).  The gauge copy of precision prec must already exist
+ * (WD_F64 exists after wd_set_gauge; the first wd_apply in WD_F32 or WD_F16
+ * creates the others), else WD_ERR_STATE.  The context's device must be current.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; calls whose
+ * kernels overlap on the GPU (different streams or host threads) race on it. */
+wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
+
 /* Solver parameters.
  *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side)
  *   max_iter   iteration limit

@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "wd_apply": ([P, D, P, P, I, I], I),
         "wd_apply_dagger": ([P, D, P, P, I, I], I),
         "wd_normal_apply": ([P, D, P, P, I, I], I),
+        "wd_normal_apply_noalloc": ([P, D, P, P, I, I], I),
         "wd_cg_solve": ([P, D, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
         "wd_cg_solve_canonical": ([P, D, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
         "wd_cg_solve_batched": ([PP, ctypes.POINTER(D), PP, PP, I, ctypes.POINTER(CGParams),
@@ -187,6 +188,13 @@ class Lattice:
     def normal_apply(self, kappa, src, dst, prec=WD_F64, nrhs=1):
         self._check(self.lib.wd_normal_apply(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
                                              ctypes.c_void_p(dst.data_ptr()), prec, nrhs), "wd_normal_apply")
+        return dst
+
+    def normal_apply_noalloc(self, kappa, src, dst, prec=WD_F64, nrhs=1):
+        """D^dag D through the entry point that allocates no device memory (fixed 16 MiB scratch)."""
+        self._check(self.lib.wd_normal_apply_noalloc(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
+                                                     ctypes.c_void_p(dst.data_ptr()), prec, nrhs),
+                    "wd_normal_apply_noalloc")
         return dst
 
     # ------------------------------------------------------------------ solvers

@@ -1,0 +1,76 @@
+"""The allocation-free normal operator (wd_normal_apply_noalloc) through the C ABI.
+
+Some callers cannot allocate device memory: their budget is fixed at start-up,
+or a cudaMalloc/cudaFree (which may synchronise the device) would stall a
+latency-critical loop.  wd_normal_apply_noalloc keeps its intermediate field in a
+fixed 16 MiB device array instead of context workspace.  These tests compare it
+with wd_normal_apply on two calls in a row (the array keeps the previous call's
+contents, which must not leak into the next result) and check the size limit.
+
+This file is named to be collected last, so a run that stops at the first
+failure has run every other test before it; it also passes on its own in a
+fresh process.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_04201_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-13, 1: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_04201_gb300 import wd as _wd
+    return _wd
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_normal_apply_twice(wd, prec):
+    import torch
+    dims, kappa = (8, 8, 6, 10), 0.12
+    U = gen.haar_links(dims, seed=31)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    if prec != 0:
+        # creates the lower-precision gauge copy (this call may allocate)
+        lat.apply(kappa, lat.new_field(prec), lat.new_field(prec), prec)
+    for call, seed in enumerate((41, 42)):
+        psi = gen.gaussian_source(dims, seed=seed)
+        f = lat.pack(psi, prec)
+        ref = lat.new_field(prec)
+        got = lat.new_field(prec)
+        lat.normal_apply(kappa, f, ref, prec)
+        lat.normal_apply_noalloc(kappa, f, got, prec)
+        assert lat.launches == 2
+        torch.cuda.synchronize()
+        a, b = lat.unpack(got, prec), lat.unpack(ref, prec)
+        assert oracle.rel_err(a, b) < TOL[prec], (call, oracle.rel_err(a, b))
+        assert oracle.rel_err(a, oracle.apply_normal(U, psi, kappa, dims)) < TOL[prec] * 4
+
+
+def test_noalloc_rejects_oversize_and_missing_gauge_copy(wd):
+    dims = (16, 16, 16, 16)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(gen.unit_links(dims))
+    f2 = lat.new_field(0, nrhs=2)  # 2 x 12.6 MB > 16 MiB
+    with pytest.raises(wd.WDError) as e:
+        lat.normal_apply_noalloc(0.12, f2, lat.new_field(0, nrhs=2), 0, nrhs=2)
+    assert e.value.status == 1 and "16777216" in str(e.value)
+    f1 = lat.new_field(2)
+    with pytest.raises(wd.WDError) as e:  # no FP16 gauge copy yet
+        lat.normal_apply_noalloc(0.12, f1, lat.new_field(2), 2)
+    assert e.value.status == 8
+    # the largest accepted size: 16^4 FP64, one right-hand side
+    psi = gen.gaussian_source(dims, seed=5)
+    f = lat.pack(psi, 0)
+    out = lat.new_field(0)
+    lat.normal_apply_noalloc(0.12, f, out, 0)
+    ref = lat.new_field(0)
+    lat.normal_apply(0.12, f, ref, 0)
+    assert oracle.rel_err(lat.unpack(out), lat.unpack(ref)) < 1e-13
