@@ -97,7 +97,11 @@ template <int P> __global__ void k_xpby(VecArgs v) {
 // thread 0 counts the reliable-update bodies run.
 template <int DUMMY = 0> __global__ void k_reliable_x(VecArgs v) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (v.state && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) v.state[1] += 1;
+    if (v.state && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        int any = 0;
+        for (int k = 0; k < v.nrhs; ++k) any |= v.sc[k].do_update;
+        if (any) v.state[1] += 1;
+    }
     if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
     C<double> x[12];
     C<float> xs[12];

@@ -7,118 +7,23 @@
 // true-residual check.  The loop condition is set on the device, so the host
 // waits only once, for the result.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "cg_kernels.cuh"
+#include "plan.cuh"
 #include "wd_host.h"
 
 using namespace wd;
 
 namespace wd {
 
-// ------------------------------------------------------------------ graph builder
-struct GraphBuilder {
-    cudaGraph_t g;
-    std::vector<cudaGraphNode_t> deps;
-    cudaError_t err = cudaSuccess;
-    long long nkernels = 0;
-
-    explicit GraphBuilder(cudaGraph_t graph) : g(graph) {}
-
-    template <class Arg>
-    void kernel(void (*f)(Arg), dim3 grid, dim3 block, const Arg &arg) {
-        if (err != cudaSuccess) return;
-        Arg copy = arg;
-        void *params[1] = {&copy};
-        cudaKernelNodeParams p{};
-        p.func = (void *)f;
-        p.gridDim = grid;
-        p.blockDim = block;
-        p.sharedMemBytes = 0;
-        p.kernelParams = params;
-        cudaGraphNode_t n;
-        err = cudaGraphAddKernelNode(&n, g, deps.data(), deps.size(), &p);
-        if (err == cudaSuccess) deps.assign(1, n);
-        ++nkernels;
-    }
-
-    // Appends a conditional node; returns its body graph.
-    cudaGraph_t conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
-        if (err != cudaSuccess) return nullptr;
-        cudaGraphNodeParams np{};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = type;
-        np.conditional.size = 1;
-        cudaGraphNode_t n;
-        err = cudaGraphAddNode(&n, g, deps.data(), nullptr, deps.size(), &np);
-        if (err != cudaSuccess) return nullptr;
-        deps.assign(1, n);
-        return np.conditional.phGraph_out[0];
-    }
-};
-
-static int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
-// Grid for a reducing Dslash: at most the blocks that fit on the machine at once.
-template <class K>
-static dim3 reduce_grid(K kernel, const Geom &g, DslashTiles t, int nrhs) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, t.site_tile * t.rhs_tile, 0);
-    if (per_sm < 1) per_sm = 1;
-    const int need = (g.V + t.site_tile - 1) / t.site_tile;
-    int cap = per_sm * num_sms();
-    return dim3(need < cap ? need : cap, (nrhs + t.rhs_tile - 1) / t.rhs_tile);
-}
-
-struct Fields {
-    void *b, *x, *db, *r, *p, *t;      // FP64
-    void *rs, *ps, *ts, *xs;            // inner precision (xs FP32)
-    Scalars *sc;
-    double *partial;
-    unsigned *counter;
-    int *state;
-};
-
-template <int P, int RECON, bool DAG, class Ep>
-static void add_dslash(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool reduce) {
-    auto k = dslash_kernel<P, RECON, DAG, Ep>;
-    dim3 block(t.site_tile, t.rhs_tile);
-    dim3 grid = reduce ? reduce_grid(k, a.g, t, a.nrhs)
-                       : dim3((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
-    gb.kernel(k, grid, block, a);
-}
-
-template <class K>
-static void add_vec(GraphBuilder &gb, K k, const VecArgs &v) {
-    gb.kernel(k, dim3((v.V + 127) / 128, v.nrhs), dim3(128), v);
-}
-
-struct SolverPlan {
-    int recon;
-    double kappa;
-    int nrhs;
-    Prec inner;
-    DslashTiles t64, tin;
-};
-
-// Build the FP64 (inner == F64) or mixed-precision solver graph.
+// Record the FP64 (inner == F64) or mixed-precision solver.  hwhile / hif are the
+// conditional handles the loop kernels set (0 for the host-driven loop).
 template <int RECON, int SP>
-static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
-                               cudaGraphExec_t *exec, std::vector<long long> &counts) {
-    cudaGraph_t graph;
-    cudaError_t e = cudaGraphCreate(&graph, 0);
-    if (e != cudaSuccess) return e;
-    GraphBuilder gb(graph);
+static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                        cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif, Plan &plan) {
+    GraphBuilder gb(&plan.setup);
     const size_t s64 = spinor_bytes(F64, c->g.Vs), sin = spinor_bytes((Prec)SP, c->g.Vs),
                  s32 = spinor_bytes(F32, c->g.Vs);
     const bool mixed = SP != F64;
@@ -153,7 +58,6 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
         a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
         add_dslash<F64, RECON, true, EpSetupR>(gb, a, pl.t64, true);
     }
-    long long n_setup = gb.nkernels;
     if (mixed) {
         VecArgs v = vb;
         v.mask = 0;
@@ -163,16 +67,11 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
         add_vec(gb, k_convert<F64, SP>, v);
         v.b = f.xs; v.b_stride = s32;
         add_vec(gb, k_zero<F32>, v);
-        n_setup = gb.nkernels;
     }
 
     // ---- loop
-    cudaGraphConditionalHandle hwhile = 0, hif = 0;
-    if (gb.err == cudaSuccess) gb.err = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
-    cudaGraph_t body = gb.conditional(hwhile, cudaGraphCondTypeWhile);
-    long long n_body = 0, n_if = 0;
-    if (gb.err == cudaSuccess) {
-        GraphBuilder bb(body);
+    {
+        GraphBuilder bb(&plan.pre);
         if (!mixed) {
             DslashArgs a = base;
             a.mask = 1;
@@ -185,7 +84,6 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
             v.a = f.r; v.a_stride = s64; v.b = f.p; v.b_stride = s64; v.cond = hwhile;
             add_vec(bb, k_xpby<F64>, v);
         } else {
-            if (bb.err == cudaSuccess) bb.err = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
             DslashArgs a = base;
             a.mask = 1;
             a.gauge = gin;
@@ -196,9 +94,9 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
             add_dslash<SP, RECON, false, EpCG1>(bb, a, pl.tin, true);
             a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
             add_dslash<SP, RECON, true, EpCG2Mixed>(bb, a, pl.tin, true);
-            cudaGraph_t ifb = bb.conditional(hif, cudaGraphCondTypeIf);
-            if (bb.err == cudaSuccess) {
-                GraphBuilder ib(ifb);
+            plan.has_if = true;
+            {
+                GraphBuilder ib(&plan.ifb);
                 VecArgs v = vb;
                 v.mask = 2;
                 v.a = f.xs; v.a_stride = s32; v.b = f.x; v.b_stride = s64;
@@ -211,19 +109,17 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
                 add_dslash<F64, RECON, true, EpReliable>(ib, r, pl.t64, true);
                 v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
                 add_vec(ib, k_convert<F64, SP>, v);
-                bb.err = ib.err;
-                n_if = ib.nkernels;
             }
+            bb.cur = &plan.post;
             VecArgs v = vb;
             v.mask = 1;
             v.a = f.rs; v.a_stride = sin; v.b = f.ps; v.b_stride = sin; v.cond = hwhile;
             add_vec(bb, k_xpby<SP>, v);
         }
-        gb.err = bb.err;
-        n_body = bb.nkernels;
     }
 
     // ---- final FP64 check: t = D x, |b - t|^2; |db - D^dag t|^2
+    gb.cur = &plan.fin;
     {
         DslashArgs a = base;
         a.mask = 0;
@@ -232,11 +128,40 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
         a.in = f.t; a.a0 = f.db;
         add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
     }
-    const long long n_final = 2;
-    e = gb.err;
+}
+
+// One CUDA graph: setup -> WHILE { pre -> IF { ifb } -> post } -> final.
+template <int RECON, int SP>
+static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                               cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    cudaGraph_t graph;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle hwhile = 0, hif = 0;
+    e = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess && SP != F64) e = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
+    Plan plan;
+    if (e == cudaSuccess) record_plan<RECON, SP>(c, pl, f, g64, gin, hwhile, hif, plan);
+    std::vector<cudaGraphNode_t> deps;
+    if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) e = add_conditional(graph, deps, hwhile, cudaGraphCondTypeWhile, &body);
+    if (e == cudaSuccess) {
+        std::vector<cudaGraphNode_t> bd;
+        e = add_chain(body, bd, plan.pre);
+        if (e == cudaSuccess && plan.has_if) {
+            cudaGraph_t ifg = nullptr;
+            e = add_conditional(body, bd, hif, cudaGraphCondTypeIf, &ifg);
+            std::vector<cudaGraphNode_t> id;
+            if (e == cudaSuccess) e = add_chain(ifg, id, plan.ifb);
+        }
+        if (e == cudaSuccess) e = add_chain(body, bd, plan.post);
+    }
+    if (e == cudaSuccess) e = add_chain(graph, deps, plan.fin);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
-    counts = {n_setup, n_body, n_if, n_final};
+    counts = {(long long)plan.setup.size(), (long long)(plan.pre.size() + plan.post.size()),
+              (long long)plan.ifb.size(), (long long)plan.fin.size()};
     return e;
 }
 
@@ -248,6 +173,44 @@ static cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, c
     case F32: return build_graph<RECON, F32>(c, pl, f, g64, gin, exec, counts);
     default: return build_graph<RECON, F16>(c, pl, f, g64, gin, exec, counts);
     }
+}
+
+template <int RECON>
+static void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan) {
+    switch (pl.inner) {
+    case F64: record_plan<RECON, F64>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F32: record_plan<RECON, F32>(c, pl, f, g64, gin, 0, 0, plan); break;
+    default: record_plan<RECON, F16>(c, pl, f, g64, gin, 0, 0, plan); break;
+    }
+}
+
+// The same plan launched kernel by kernel from the host; the active flags are read
+// back every `chunk` iterations.  Loop kernels of converged rows return at once,
+// so iterations launched after convergence change nothing.
+static cudaError_t run_host_loop(wd_ctx *c, const Plan &plan, const Fields &f, int nrhs, int max_iter,
+                                 long long *launched) {
+    const int chunk = 4;
+    std::vector<Scalars> h(nrhs);
+    cudaError_t e = launch_chain(plan.setup, c->stream);
+    long long n = (long long)plan.setup.size();
+    int it = 0;
+    while (e == cudaSuccess && it <= max_iter + 1) {
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k, ++it) {
+            e = launch_chain(plan.pre, c->stream);
+            if (e == cudaSuccess) e = launch_chain(plan.ifb, c->stream);
+            if (e == cudaSuccess) e = launch_chain(plan.post, c->stream);
+            n += (long long)(plan.pre.size() + plan.ifb.size() + plan.post.size());
+        }
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        bool any = false;
+        for (int r = 0; r < nrhs; ++r) any |= h[r].active != 0;
+        if (!any) break;
+    }
+    if (e == cudaSuccess) e = launch_chain(plan.fin, c->stream);
+    *launched = n + (long long)plan.fin.size();
+    return e;
 }
 
 wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm,
@@ -305,18 +268,27 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     char key[256];
     snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
              pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile);
-    cudaGraphExec_t exec;
-    auto it = c->graphs.find(key);
-    if (it == c->graphs.end()) {
-        std::vector<long long> counts;
-        cudaError_t e = c->recon == 12 ? build_for<12>(c, pl, f, g64, gin, &exec, counts)
-                                       : build_for<18>(c, pl, f, g64, gin, &exec, counts);
-        if (e != cudaSuccess) return cuda_fail(c, e, "building the CG graph");
-        c->graphs[key] = exec;
-        c->graph_info[key] = counts;
-        WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 256, c->stream));
+    const char *loop_env = getenv("WD_CG_LOOP");
+    const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
+    cudaGraphExec_t exec = nullptr;
+    Plan hplan;
+    if (host_loop) {
+        if (c->recon == 12) record_for<12>(c, pl, f, g64, gin, hplan);
+        else record_for<18>(c, pl, f, g64, gin, hplan);
+        WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 64, c->stream));
     } else {
-        exec = (cudaGraphExec_t)it->second;
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            std::vector<long long> counts;
+            cudaError_t e = c->recon == 12 ? build_for<12>(c, pl, f, g64, gin, &exec, counts)
+                                           : build_for<18>(c, pl, f, g64, gin, &exec, counts);
+            if (e != cudaSuccess) return cuda_fail(c, e, "building the CG graph");
+            c->graphs[key] = exec;
+            c->graph_info[key] = counts;
+            WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 256, c->stream));
+        } else {
+            exec = (cudaGraphExec_t)it->second;
+        }
     }
 
     // per-RHS state
@@ -338,7 +310,9 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     WD_CUDA(c, cudaEventCreate(&e0));
     WD_CUDA(c, cudaEventCreate(&e1));
     WD_CUDA(c, cudaEventRecord(e0, c->stream));
-    WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
+    long long host_launched = 0;
+    if (host_loop) WD_CUDA(c, run_host_loop(c, hplan, f, nrhs, prm->max_iter, &host_launched));
+    else WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
     WD_CUDA(c, cudaEventRecord(e1, c->stream));
     WD_CUDA(c, cudaMemcpyAsync(x, f.x, s64, cudaMemcpyDeviceToDevice, c->stream));
     WD_CUDA(c, cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream));
@@ -349,8 +323,12 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const std::vector<long long> &cnt = c->graph_info[key];
-    c->launches = cnt[0] + (long long)st[0] * cnt[1] + (long long)st[1] * cnt[2] + cnt[3];
+    if (host_loop) {
+        c->launches = host_launched;
+    } else {
+        const std::vector<long long> &cnt = c->graph_info[key];
+        c->launches = cnt[0] + (long long)st[0] * cnt[1] + (long long)st[1] * cnt[2] + cnt[3];
+    }
 
     wd_status worst = WD_OK;
     for (int r = 0; r < nrhs; ++r) {

@@ -39,6 +39,7 @@ struct DslashArgs {
     unsigned *counter;         // last-block ticket
     unsigned long long cond;   // cudaGraphConditionalHandle to set (0 = none)
     int *state;                // solver-wide counters
+    const int *run_flag;       // when set and zero, the whole launch returns at once
 };
 
 template <class R> __device__ __forceinline__ const void *rhs_ptr(const void *b, size_t stride, int r) {
@@ -157,6 +158,7 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
 template <int P, int RECON, bool DAG, class Ep>
 __global__ void __launch_bounds__(256) dslash_kernel(DslashArgs a) {
     using R = typename Real<P>::T;
+    if (a.run_flag && *a.run_flag == 0) return;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     const bool row = r < a.nrhs && row_on(a.sc, a.mask, r);
     const void *in = rhs_ptr<R>(a.in, a.in_stride, r < a.nrhs ? r : 0);

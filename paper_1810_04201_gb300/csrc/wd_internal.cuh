@@ -234,8 +234,8 @@ template <int RECON> struct LinkIO<F16, RECON> {
 // Deterministic block reduction of NV doubles per row of a (SB x RT) block.  SB is a
 // power of two (16 .. 256) and SB * RT a multiple of 32, so the shuffle groups of
 // min(SB, 32) lanes never straddle two rows.  Result valid in threadIdx.x == 0.
-// smem: at least RT * 8 * NV doubles.
-template <int NV>
+// smem: at least RT * MAXW * NV doubles, MAXW >= ceil(SB / 32).
+template <int NV, int MAXW = 8>
 __device__ __forceinline__ void block_reduce_rows(double (&v)[NV], double *smem) {
     const int SB = blockDim.x;
     const int width = SB < 32 ? SB : 32;
@@ -243,7 +243,7 @@ __device__ __forceinline__ void block_reduce_rows(double (&v)[NV], double *smem)
     for (int k = 0; k < NV; ++k)
         for (int o = width >> 1; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (SB + 31) >> 5;
-    double *row = smem + (size_t)threadIdx.y * 8 * NV;
+    double *row = smem + (size_t)threadIdx.y * MAXW * NV;
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) row[w * NV + k] = v[k];

@@ -141,3 +141,59 @@ def test_cg_canonical_host_buffers(wd):
     res, st = lat.cg_canonical(kappa, bt, xt, tol=1e-10)
     x_ref, _ = ref_solution(U, b, kappa, dims)
     assert st == 0 and oracle.rel_err(xt.numpy(), x_ref) < 1e-9
+
+
+@pytest.mark.parametrize("k,recon,seed", [(12, 18, 7), (5, 12, 8), (1, 18, 9)])
+def test_block_cg(wd, k, recon, seed):
+    """Block CG over k right-hand sides: every column matches the oracle solution."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = gen.haar_links(dims, seed=seed)
+    B = gen.propagator_sources(dims)[:k] if k == 12 else gen.gaussian_source(dims, seed=seed, nrhs=k)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=recon)
+    fb, fx = lat.pack(B), lat.new_field(nrhs=k)
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, nrhs=k, block=1)
+    assert st == 0, res
+    X = lat.unpack(fx, nrhs=k, squeeze=False)
+    for j in sorted({0, k // 2, k - 1}):
+        x_ref, _ = ref_solution(U, B[j], kappa, dims)
+        assert oracle.rel_err(X[j], x_ref) < 1e-9
+    assert all(r["true_rel_resid"] <= 1e-10 for r in res)
+    if k == 12:
+        fy = lat.new_field(nrhs=k)
+        res1, _ = lat.cg(kappa, fb, fy, tol=1e-10, nrhs=k, block=0)
+        assert res[0]["iters"] < max(r["iters"] for r in res1)
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+def test_host_loop_matches_graph(wd, inner, monkeypatch):
+    """The host-driven loop (WD_CG_LOOP=host) launches the same kernels: same result, bit for bit."""
+    dims, kappa = (4, 4, 6, 4), 0.12
+    U = gen.haar_links(dims, seed=3)
+    b = gen.gaussian_source(dims, seed=4)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb = lat.pack(b)
+    fx1, fx2 = lat.new_field(), lat.new_field()
+    r1, _ = lat.cg(kappa, fb, fx1, tol=1e-10, inner=inner)
+    monkeypatch.setenv("WD_CG_LOOP", "host")
+    r2, _ = lat.cg(kappa, fb, fx2, tol=1e-10, inner=inner)
+    assert r1[0]["iters"] == r2[0]["iters"]
+    np.testing.assert_array_equal(lat.unpack(fx1), lat.unpack(fx2))
+
+
+def test_autotune_keeps_results(wd):
+    dims, kappa = (8, 8, 8, 8), 0.12
+    U = gen.haar_links(dims, seed=5)
+    psi = gen.gaussian_source(dims, seed=6, nrhs=4)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    f = lat.pack(psi)
+    o1 = lat.new_field(nrhs=4)
+    lat.apply(kappa, f, o1, nrhs=4)
+    st, rt = lat.autotune(0, 4)
+    assert st in (16, 32, 64, 128, 256) and 1 <= rt <= 4 and (st * rt) % 32 == 0
+    o2 = lat.new_field(nrhs=4)
+    lat.apply(kappa, f, o2, nrhs=4)
+    # the per-site arithmetic does not depend on the launch shape
+    np.testing.assert_array_equal(lat.unpack(o1, nrhs=4), lat.unpack(o2, nrhs=4))
