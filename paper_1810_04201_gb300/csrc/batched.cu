@@ -1,0 +1,562 @@
+// Batched solver: many independent lattices (own dims, links, kappa, source) in
+// one persistent cooperative kernel, mixed-precision CG with FP64 reliable
+// updates (section 2.3: a new U and eta per solve; section 2.2: CG on the normal
+// equations).
+//
+// Work list: every lattice is cut into tiles of kTile sites; the tiles of all
+// lattices form one list that the resident blocks walk (block b takes tiles b,
+// b + grid, ...).  A CG step is a sequence of phases separated by grid barriers;
+// per-lattice reductions use one partial per tile and the block that finishes a
+// lattice's last tile sums them in tile order (deterministic) and advances that
+// lattice's scalar recursion, so every phase needs exactly one barrier.
+// Converged lattices drop out of the list; the kernel ends when none is left.
+//
+// Grid barriers spin on a generation counter with a cycle limit: when it runs
+// out the waiting block raises an error flag, every block leaves the kernel at
+// its next barrier, and the host reports WD_ERR_TIMEOUT for every lattice.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include "cg_kernels.cuh"
+#include "plan.cuh"
+#include "wd_host.h"
+
+using namespace wd;
+
+namespace wd {
+
+constexpr int kTile = 128;
+
+struct LatDesc {
+    Geom g;
+    double kappa;
+    const void *g64, *gs;
+    size_t gdir64, gdirs;
+    void *b, *x, *db, *r, *t, *rs, *ps, *ts, *xs;
+    int tile0, ntiles;
+};
+
+struct BatchArgs {
+    const LatDesc *lat;
+    Scalars *sc;         // per lattice
+    unsigned *lcount;    // per lattice tile tickets
+    double *tpart;       // per tile partials (2 values)
+    const int *tile_lat; // lattice of each tile
+    int ntiles, nlat, max_iter;
+    unsigned *bar_count, *bar_gen;
+    int *flags;          // [0] error, [1] any reliable update pending, [2] iterations run, [3] never set
+    long long spin_limit;
+    int stall_test;      // block 0 first waits on flags[3], which nothing sets
+};
+
+// Bounded grid barrier (all blocks are co-resident: cooperative launch).
+__device__ bool grid_barrier(const BatchArgs &a) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = a.bar_gen;
+        volatile int *err = a.flags;
+        const unsigned my = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(a.bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *a.bar_count = 0;
+            __threadfence();
+            atomicAdd(a.bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == my) {
+                if (*err) break;
+                if (clock64() - t0 > a.spin_limit) {
+                    atomicExch(a.flags, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = *err == 0;
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Block reduction of NV values, one partial per tile, and the per-lattice finish
+// in the block that completes the lattice's last tile (`fin(l, totals)`, thread 0).
+template <int NV, class F>
+__device__ void tile_reduce(const BatchArgs &a, const LatDesc &L, int g, int l, double (&v)[NV], F &&fin) {
+    __shared__ double red[8 * NV];
+    __shared__ int last;
+    block_reduce_rows<NV>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a.tpart[(size_t)g * 2 + k] = v[k];
+        __threadfence();
+        last = atomicAdd(a.lcount + l, 1u) == (unsigned)L.ntiles - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0.0;
+    for (int i = threadIdx.x; i < L.ntiles; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += __ldcg(a.tpart + (size_t)(L.tile0 + i) * 2 + k);
+    __syncthreads();
+    block_reduce_rows<NV>(s, red);
+    if (threadIdx.x == 0) {
+        a.lcount[l] = 0;
+        fin(l, s);
+    }
+    __syncthreads();
+}
+
+// One phase: walk the tiles of the lattices selected by `want(sc)`.
+template <class W, class F>
+__device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
+    __shared__ LatDesc L;
+    __shared__ int run;
+    for (int g = blockIdx.x; g < a.ntiles; g += gridDim.x) {
+        const int l = a.tile_lat[g];
+        if (threadIdx.x == 0) {
+            run = want(a.sc[l]);
+            if (run) L = a.lat[l];
+        }
+        __syncthreads();
+        if (run) {
+            const int s = (g - L.tile0) * kTile + threadIdx.x;
+            body(L, g, l, s, s < L.g.V);
+        }
+        __syncthreads();
+    }
+}
+
+template <int SP, int RECON>
+__global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
+    using RS = typename Real<SP>::T;
+    auto all = [](const Scalars &) { return 1; };
+    auto active = [](const Scalars &c) { return c.active; };
+    auto updating = [](const Scalars &c) { return c.active && c.do_update; };
+
+    if (a.stall_test && blockIdx.x == 0 && threadIdx.x == 0) {
+        // a wait that runs out: nothing ever sets flags[3]
+        const long long t0 = clock64();
+        volatile int *never = a.flags + 3;
+        while (*never == 0 && clock64() - t0 <= a.spin_limit) __nanosleep(64);
+        if (*never == 0) atomicExch(a.flags, 1);
+    }
+
+    // ---- setup (FP64): db = D^dag b, |db|^2, |b|^2 ; t = D x0
+    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+        double v[2] = {0.0, 0.0};
+        if (valid) {
+            C<double> acc[12], p[12];
+            hopping<F64, RECON, true, false>(L.g, L.b, L.g64, L.gdir64, s, acc);
+            SpinorIO<F64>::template load<false>(L.b, L.g.Vs, s, p);
+            v[1] = norm2_of(p);
+            xpay_site(p, acc, L.kappa);
+            v[0] = norm2_of(p);
+            SpinorIO<F64>::store(L.db, L.g.Vs, s, p);
+            hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
+            SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
+            xpay_site(p, acc, L.kappa);
+            SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
+        }
+        tile_reduce<2>(a, L, g, l, v, [&](int l2, const double *t) {
+            Scalars &c = a.sc[l2];
+            c.rhs2 = t[0];
+            c.b2 = t[1];
+            c.tol2 *= t[0];
+        });
+    });
+    if (!grid_barrier(a)) return;
+    // r = db - D^dag t ; rs = ps = r (inner precision) ; xs = 0 ; rho = |r|^2
+    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+        double v[1] = {0.0};
+        if (valid) {
+            C<double> acc[12], q[12], d[12];
+            hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
+            SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
+            xpay_site(q, acc, L.kappa);
+            SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+            v[0] = norm2_of(d);
+            SpinorIO<F64>::store(L.r, L.g.Vs, s, d);
+            C<RS> w[12];
+            C<float> z[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                w[c] = C<RS>{RS(d[c].re), RS(d[c].im)};
+                z[c] = C<float>{0.f, 0.f};
+            }
+            SpinorIO<SP>::store(L.rs, L.g.Vs, s, w);
+            SpinorIO<SP>::store(L.ps, L.g.Vs, s, w);
+            SpinorIO<F32>::store(L.xs, L.g.Vs, s, z);
+        }
+        tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
+            Scalars &c = a.sc[l2];
+            c.rho = t[0];
+            c.rmax2 = t[0];
+            if (!isfinite(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; }
+            else if (t[0] <= c.tol2) { c.status = WD_OK; c.active = 0; }
+        });
+    });
+    if (!grid_barrier(a)) return;
+
+    for (int it = 0; it < a.max_iter + 2; ++it) {
+        int any = 0;
+        for (int l = 0; l < a.nlat; ++l) any |= a.sc[l].active;
+        if (!any) break;
+        if (threadIdx.x == 0 && blockIdx.x == 0) a.flags[2] = it + 1;
+        // A: ts = D ps ; pAp = |ts|^2 ; alpha
+        for_tiles(a, active, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+            double v[1] = {0.0};
+            if (valid) {
+                C<RS> acc[12], p[12];
+                hopping<SP, RECON, false, false>(L.g, L.ps, L.gs, L.gdirs, s, acc);
+                SpinorIO<SP>::template load<false>(L.ps, L.g.Vs, s, p);
+                xpay_site(p, acc, RS(L.kappa));
+                v[0] = norm2_of(p);
+                SpinorIO<SP>::store(L.ts, L.g.Vs, s, p);
+            }
+            tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
+                Scalars &c = a.sc[l2];
+                c.pAp = t[0];
+                if (!isfinite(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; }
+                else if (!(t[0] > 0.0)) { c.status = WD_ERR_BREAKDOWN; c.active = 0; }
+                else c.alpha = c.rho / t[0];
+            });
+        });
+        if (!grid_barrier(a)) return;
+        // B: q = D^dag ts ; rs -= alpha q ; xs += alpha ps ; rho' = |rs|^2 ; decide
+        for_tiles(a, active, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+            double v[1] = {0.0};
+            if (valid) {
+                const RS alpha = RS(a.sc[l].alpha);
+                C<RS> acc[12], q[12], w[12];
+                hopping<SP, RECON, true, false>(L.g, L.ts, L.gs, L.gdirs, s, acc);
+                SpinorIO<SP>::template load<false>(L.ts, L.g.Vs, s, q);
+                xpay_site(q, acc, RS(L.kappa));
+                SpinorIO<SP>::template load<false>(L.rs, L.g.Vs, s, w);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) w[c] = C<RS>{w[c].re - alpha * q[c].re, w[c].im - alpha * q[c].im};
+                v[0] = norm2_of(w);
+                SpinorIO<SP>::store(L.rs, L.g.Vs, s, w);
+                SpinorIO<SP>::template load<false>(L.ps, L.g.Vs, s, q);
+                C<float> xs[12];
+                SpinorIO<F32>::template load<false>(L.xs, L.g.Vs, s, xs);
+#pragma unroll
+                for (int c = 0; c < 12; ++c)
+                    xs[c] = C<float>{xs[c].re + float(alpha * q[c].re), xs[c].im + float(alpha * q[c].im)};
+                SpinorIO<F32>::store(L.xs, L.g.Vs, s, xs);
+            }
+            tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
+                Scalars &c = a.sc[l2];
+                const double rn = t[0];
+                c.iter += 1;
+                if (!isfinite(rn)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+                if (rn <= c.tol2 || rn < c.delta2 * c.rmax2 || c.iter >= c.max_iter) {
+                    c.do_update = 1;
+                    atomicExch(a.flags + 1, 1);
+                } else {
+                    c.beta = rn / c.rho;
+                    c.rho = rn;
+                    c.rmax2 = fmax(c.rmax2, rn);
+                }
+            });
+        });
+        if (!grid_barrier(a)) return;
+        if (*(volatile int *)(a.flags + 1)) {
+            // C1: x += xs ; xs = 0  (FP64 solution accumulation)
+            for_tiles(a, updating, [&](const LatDesc &L, int, int, int s, bool valid) {
+                if (!valid) return;
+                C<double> x[12];
+                C<float> xs[12];
+                SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, x);
+                SpinorIO<F32>::template load<false>(L.xs, L.g.Vs, s, xs);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    x[c] = C<double>{x[c].re + (double)xs[c].re, x[c].im + (double)xs[c].im};
+                    xs[c] = C<float>{0.f, 0.f};
+                }
+                SpinorIO<F64>::store(L.x, L.g.Vs, s, x);
+                SpinorIO<F32>::store(L.xs, L.g.Vs, s, xs);
+            });
+            if (!grid_barrier(a)) return;
+            // C2: t = D x (FP64)
+            for_tiles(a, updating, [&](const LatDesc &L, int, int, int s, bool valid) {
+                if (!valid) return;
+                C<double> acc[12], p[12];
+                hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
+                SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
+                xpay_site(p, acc, L.kappa);
+                SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
+            });
+            if (!grid_barrier(a)) return;
+            // C3: r = db - D^dag t ; rho = |r|^2 (the true residual of the normal equations)
+            for_tiles(a, updating, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+                double v[1] = {0.0};
+                if (valid) {
+                    C<double> acc[12], q[12], d[12];
+                    hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
+                    SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
+                    xpay_site(q, acc, L.kappa);
+                    SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+                    v[0] = norm2_of(d);
+                    SpinorIO<F64>::store(L.r, L.g.Vs, s, d);
+                }
+                tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
+                    Scalars &c = a.sc[l2];
+                    const double rt = t[0];
+                    c.reliable += 1;
+                    if (!isfinite(rt)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+                    c.beta = rt / c.rho;
+                    c.rho = rt;
+                    c.rmax2 = rt;
+                    if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
+                    else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+                });
+            });
+            if (!grid_barrier(a)) return;
+        }
+        // D: rs = r (after a reliable update) ; ps = rs + beta ps
+        for_tiles(a, active, [&](const LatDesc &L, int, int l, int s, bool valid) {
+            if (!valid) return;
+            const Scalars &c = a.sc[l];
+            const RS beta = RS(c.beta);
+            C<RS> w[12], p[12];
+            if (c.do_update) {
+                C<double> d[12];
+                SpinorIO<F64>::template load<false>(L.r, L.g.Vs, s, d);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) w[k] = C<RS>{RS(d[k].re), RS(d[k].im)};
+                SpinorIO<SP>::store(L.rs, L.g.Vs, s, w);
+            } else {
+                SpinorIO<SP>::template load<false>(L.rs, L.g.Vs, s, w);
+            }
+            SpinorIO<SP>::template load<false>(L.ps, L.g.Vs, s, p);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) p[k] = C<RS>{w[k].re + beta * p[k].re, w[k].im + beta * p[k].im};
+            SpinorIO<SP>::store(L.ps, L.g.Vs, s, p);
+        });
+        if (!grid_barrier(a)) return;
+        // clear the pending flags (one block owns them), then a barrier before the next step
+        if (blockIdx.x == 0) {
+            for (int l = threadIdx.x; l < a.nlat; l += blockDim.x) a.sc[l].do_update = 0;
+            if (threadIdx.x == 0) a.flags[1] = 0;
+        }
+        if (!grid_barrier(a)) return;
+    }
+
+    // ---- final FP64 check: t = D x, |b - t|^2 ; |db - D^dag t|^2
+    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+        double v[1] = {0.0};
+        if (valid) {
+            C<double> acc[12], p[12], b[12];
+            hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
+            SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
+            xpay_site(p, acc, L.kappa);
+            SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
+            SpinorIO<F64>::template load<false>(L.b, L.g.Vs, s, b);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) b[c] = csub(b[c], p[c]);
+            v[0] = norm2_of(b);
+        }
+        tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) { a.sc[l2].true_b2 = t[0]; });
+    });
+    if (!grid_barrier(a)) return;
+    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+        double v[1] = {0.0};
+        if (valid) {
+            C<double> acc[12], q[12], d[12];
+            hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
+            SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
+            xpay_site(q, acc, L.kappa);
+            SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+            v[0] = norm2_of(d);
+        }
+        tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) { a.sc[l2].true_n2 = t[0]; });
+    });
+}
+
+template <int SP, int RECON>
+static cudaError_t launch_batched(BatchArgs &a, cudaStream_t st, int *grid_out) {
+    auto k = k_batched_cg<SP, RECON>;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTile, 0);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = per_sm * sms;
+    if (grid > a.ntiles) grid = a.ntiles;
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    *grid_out = grid;
+    // one persistent cooperative launch, captured in a CUDA graph
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTile);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cfg.stream = cap;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t el = cudaLaunchKernelEx(&cfg, k, a);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (el != cudaSuccess) e = el;
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return e;
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphLaunch(exec, st);
+    cudaGraphExecDestroy(exec);
+    return e;
+}
+
+}  // namespace wd
+
+extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const void *const *b,
+                                         void *const *x, int n, const wd_cg_params *prm, wd_cg_result *res) {
+    if (!ctxs || n < 1 || !ctxs[0]) return WD_ERR_ARG;
+    wd_ctx *c0 = ctxs[0];
+    c0->launches = 0;
+    if (!kappas || !b || !x || !prm || !res) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: null argument");
+    if (prm->inner_prec != WD_F32 && prm->inner_prec != WD_F16)
+        return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: inner_prec must be WD_F32 or WD_F16");
+    if ((prm->nrhs > 1) || !(prm->tol > 0)) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: bad nrhs or tol");
+    const Prec sp = (Prec)prm->inner_prec;
+    std::vector<LatDesc> lat(n);
+    std::vector<int> tile_lat;
+    int ntiles = 0;
+    for (int i = 0; i < n; ++i) {
+        wd_ctx *c = ctxs[i];
+        if (!c || !b[i] || !x[i] || !std::isfinite(kappas[i]))
+            return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: null context, field or bad kappa");
+        if (c->device != c0->device) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: contexts on different devices");
+        if (c->recon != c0->recon) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: mixed link compression");
+        wd_status s;
+        const void *g64, *gs;
+        if ((s = gauge_get(c, F64, &g64)) != WD_OK) return fail(c0, s, c->last_error);
+        if ((s = gauge_get(c, sp, &gs)) != WD_OK) return fail(c0, s, c->last_error);
+        LatDesc &L = lat[i];
+        L.g = c->g;
+        L.kappa = kappas[i];
+        L.g64 = g64;
+        L.gs = gs;
+        L.gdir64 = gauge_dir_bytes(c, F64);
+        L.gdirs = gauge_dir_bytes(c, sp);
+        const size_t f64 = spinor_bytes(F64, c->g.Vs), fsp = spinor_bytes(sp, c->g.Vs),
+                     f32 = spinor_bytes(F32, c->g.Vs);
+        void **p64[4] = {&L.x, &L.db, &L.r, &L.t};
+        const char *n64[4] = {"bt_x", "bt_db", "bt_r", "bt_t"};
+        for (int k = 0; k < 4; ++k)
+            if ((s = ws_get(c, n64[k], f64, p64[k])) != WD_OK) return fail(c0, s, c->last_error);
+        void **psp[3] = {&L.rs, &L.ps, &L.ts};
+        const char *nsp[3] = {"bt_rs", "bt_ps", "bt_ts"};
+        for (int k = 0; k < 3; ++k)
+            if ((s = ws_get(c, std::string(nsp[k]) + (sp == F32 ? "32" : "16"), fsp, psp[k])) != WD_OK)
+                return fail(c0, s, c->last_error);
+        if ((s = ws_get(c, "bt_xs", f32, &L.xs)) != WD_OK) return fail(c0, s, c->last_error);
+        L.b = const_cast<void *>(b[i]);
+        L.tile0 = ntiles;
+        L.ntiles = (c->g.V + kTile - 1) / kTile;
+        ntiles += L.ntiles;
+        tile_lat.insert(tile_lat.end(), L.ntiles, i);
+    }
+    // batch-wide buffers live in the first context
+    cudaStream_t st = c0->stream;
+    void *d_lat, *d_sc, *d_cnt, *d_part, *d_tl, *d_bar;
+    wd_status s;
+    if ((s = ws_get(c0, "bt_lat", sizeof(LatDesc) * n, &d_lat)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_sc", sizeof(Scalars) * n, &d_sc)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_cnt", sizeof(unsigned) * n, &d_cnt)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_part", sizeof(double) * 2 * ntiles, &d_part)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_tl", sizeof(int) * ntiles, &d_tl)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_bar", 256, &d_bar)) != WD_OK) return s;
+    std::vector<Scalars> h(n);
+    const double delta = prm->delta > 0 ? prm->delta : 0.1;
+    for (int i = 0; i < n; ++i) {
+        std::memset(&h[i], 0, sizeof(Scalars));
+        h[i].tol2 = prm->tol * prm->tol;
+        h[i].max_iter = prm->max_iter;
+        h[i].delta2 = delta * delta;
+        h[i].active = 1;
+        h[i].status = WD_ERR_NOT_CONVERGED;
+    }
+    WD_CUDA(c0, cudaMemcpyAsync(d_lat, lat.data(), sizeof(LatDesc) * n, cudaMemcpyHostToDevice, st));
+    WD_CUDA(c0, cudaMemcpyAsync(d_sc, h.data(), sizeof(Scalars) * n, cudaMemcpyHostToDevice, st));
+    WD_CUDA(c0, cudaMemcpyAsync(d_tl, tile_lat.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, st));
+    WD_CUDA(c0, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * n, st));
+    WD_CUDA(c0, cudaMemsetAsync(d_bar, 0, 256, st));
+    for (int i = 0; i < n; ++i)
+        WD_CUDA(c0, cudaMemcpyAsync(lat[i].x, x[i], spinor_bytes(F64, lat[i].g.Vs), cudaMemcpyDeviceToDevice, st));
+
+    BatchArgs a{};
+    a.lat = (const LatDesc *)d_lat;
+    a.sc = (Scalars *)d_sc;
+    a.lcount = (unsigned *)d_cnt;
+    a.tpart = (double *)d_part;
+    a.tile_lat = (const int *)d_tl;
+    a.ntiles = ntiles;
+    a.nlat = n;
+    a.max_iter = prm->max_iter;
+    a.bar_count = (unsigned *)d_bar;
+    a.bar_gen = (unsigned *)d_bar + 16;
+    a.flags = (int *)d_bar + 32;
+    const char *stall = getenv("WD_BATCH_STALL_TEST");
+    a.stall_test = stall && std::strcmp(stall, "1") == 0;
+    // about one second at GB300 clocks; a tenth of that for the stalled-wait test
+    a.spin_limit = a.stall_test ? 200000000ll : 2000000000ll;
+
+    cudaEvent_t e0, e1;
+    WD_CUDA(c0, cudaEventCreate(&e0));
+    WD_CUDA(c0, cudaEventCreate(&e1));
+    WD_CUDA(c0, cudaEventRecord(e0, st));
+    int grid = 0;
+    cudaError_t e;
+    if (c0->recon == 12) e = sp == F32 ? launch_batched<F32, 12>(a, st, &grid) : launch_batched<F16, 12>(a, st, &grid);
+    else e = sp == F32 ? launch_batched<F32, 18>(a, st, &grid) : launch_batched<F16, 18>(a, st, &grid);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "batched persistent CG launch");
+    WD_CUDA(c0, cudaEventRecord(e1, st));
+    for (int i = 0; i < n; ++i)
+        WD_CUDA(c0, cudaMemcpyAsync(x[i], lat[i].x, spinor_bytes(F64, lat[i].g.Vs), cudaMemcpyDeviceToDevice, st));
+    int flags[4];
+    WD_CUDA(c0, cudaMemcpyAsync(h.data(), d_sc, sizeof(Scalars) * n, cudaMemcpyDeviceToHost, st));
+    WD_CUDA(c0, cudaMemcpyAsync(flags, (int *)d_bar + 32, sizeof flags, cudaMemcpyDeviceToHost, st));
+    WD_CUDA(c0, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c0->launches = 1;
+    wd_status worst = WD_OK;
+    for (int i = 0; i < n; ++i) {
+        res[i].iters = h[i].iter;
+        res[i].reliable_updates = h[i].reliable;
+        res[i].true_rel_resid = h[i].rhs2 > 0 ? std::sqrt(h[i].true_n2 / h[i].rhs2) : std::sqrt(h[i].true_n2);
+        res[i].true_rel_resid_b = h[i].b2 > 0 ? std::sqrt(h[i].true_b2 / h[i].b2) : std::sqrt(h[i].true_b2);
+        res[i].seconds = ms * 1e-3;
+        res[i].status = flags[0] ? WD_ERR_TIMEOUT : h[i].status;
+        if (res[i].status != WD_OK && worst == WD_OK) worst = (wd_status)res[i].status;
+    }
+    if (worst != WD_OK) c0->last_error = std::string("wd_cg_solve_batched: ") + wd_status_string(worst);
+    return worst;
+}

@@ -104,7 +104,7 @@ __device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6],
         }
 }
 
-template <int P, int RECON, bool DAG, int MU>
+template <int P, int RECON, bool DAG, int MU, bool NC = true>
 __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const char *gdir, int s, int c,
                                         C<typename Real<P>::T> (&acc)[12]) {
     using R = typename Real<P>::T;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     {
         const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
         C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::load(in, g.Vs, sf, p);
+        SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
         project<MU, SF>(p, h);
         LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
         su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     {
         const int sb = (c == 0) ? s + (L - 1) * st : s - st;
         C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::load(in, g.Vs, sb, p);
+        SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
         project<MU, -SF>(p, h);
         LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
         su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
@@ -131,7 +131,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
 }
 
 // acc = sum over the 8 hops (the bracket of Eq. (1)) at site s of field `in`.
-template <int P, int RECON, bool DAG>
+template <int P, int RECON, bool DAG, bool NC = true>
 __device__ __forceinline__ void hopping(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes, int s,
                                         C<typename Real<P>::T> (&acc)[12]) {
     using R = typename Real<P>::T;
@@ -143,10 +143,10 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
     const int z = rem % g.L[2];
     const int t = rem / g.L[2];
     const char *gb = reinterpret_cast<const char *>(gauge);
-    hop_dir<P, RECON, DAG, 0>(g, in, gb, s, x, acc);
-    hop_dir<P, RECON, DAG, 1>(g, in, gb + gdir_bytes, s, y, acc);
-    hop_dir<P, RECON, DAG, 2>(g, in, gb + 2 * gdir_bytes, s, z, acc);
-    hop_dir<P, RECON, DAG, 3>(g, in, gb + 3 * gdir_bytes, s, t, acc);
+    hop_dir<P, RECON, DAG, 0, NC>(g, in, gb, s, x, acc);
+    hop_dir<P, RECON, DAG, 1, NC>(g, in, gb + gdir_bytes, s, y, acc);
+    hop_dir<P, RECON, DAG, 2, NC>(g, in, gb + 2 * gdir_bytes, s, z, acc);
+    hop_dir<P, RECON, DAG, 3, NC>(g, in, gb + 3 * gdir_bytes, s, t, acc);
 }
 
 // Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks

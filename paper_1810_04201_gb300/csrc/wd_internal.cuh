@@ -73,16 +73,25 @@ inline size_t gauge_bytes(Prec p, int recon, int Vs) { return 4 * round_up(link_
 template <int P> struct Real { using T = float; };
 template <> struct Real<F64> { using T = double; };
 
+// Global loads: the read-only path (ld.global.nc) for fields a launch only reads,
+// plain coherent loads (NC = false) for fields that other blocks of the same
+// persistent launch write between grid barriers.
+template <bool NC, class T> __device__ __forceinline__ T ldx(const T *p) {
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
 // Spinor load/store: v[spin*3 + colour]
 template <int P> struct SpinorIO;
 
 template <> struct SpinorIO<F64> {
     using R = double;
+    template <bool NC = true>
     static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
         const double2 *p = reinterpret_cast<const double2 *>(base) + s;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-            double2 t = __ldg(p + (size_t)c * Vs);
+            double2 t = ldx<NC>(p + (size_t)c * Vs);
             v[c] = C<R>{t.x, t.y};
         }
     }
@@ -95,11 +104,12 @@ template <> struct SpinorIO<F64> {
 
 template <> struct SpinorIO<F32> {
     using R = float;
+    template <bool NC = true>
     static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
         const float4 *p = reinterpret_cast<const float4 *>(base) + s;
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            float4 t = __ldg(p + (size_t)j * Vs);
+            float4 t = ldx<NC>(p + (size_t)j * Vs);
             v[2 * j] = C<R>{t.x, t.y};
             v[2 * j + 1] = C<R>{t.z, t.w};
         }
@@ -125,12 +135,13 @@ template <> struct SpinorIO<F16> {
     static __device__ __forceinline__ const float *norms(const void *base, int Vs) {
         return reinterpret_cast<const float *>(reinterpret_cast<const char *>(base) + (size_t)3 * Vs * 16);
     }
+    template <bool NC = true>
     static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
         const uint4 *p = reinterpret_cast<const uint4 *>(base) + s;
-        const float nrm = __ldg(norms(base, Vs) + s);
+        const float nrm = ldx<NC>(norms(base, Vs) + s);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            uint4 t = __ldg(p + (size_t)j * Vs);
+            uint4 t = ldx<NC>(p + (size_t)j * Vs);
             float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
             v[4 * j + 0] = C<R>{a.x * nrm, a.y * nrm};
             v[4 * j + 1] = C<R>{b.x * nrm, b.y * nrm};

@@ -1,0 +1,79 @@
+"""The batched persistent solver: many lattices of uneven size and kappa in one
+cooperative launch, each solution checked against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_04201_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 4, 4, 4), (4, 4, 4, 8), (6, 6, 6, 6), (4, 6, 4, 8), (8, 8, 8, 8), (2, 4, 4, 4), (6, 6, 6, 8)]
+
+
+@pytest.fixture(scope="module")
+def wd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1810_04201_gb300 import wd as _wd
+    return _wd
+
+
+def make_batch(wd, recon=18):
+    kappas = [0.10 + 0.025 * u for u in gen.uniform(5, 5, 0, len(SHAPES))]
+    lats, bs, xs, inputs = [], [], [], []
+    for i, dims in enumerate(SHAPES):
+        U = gen.haar_links(dims, seed=100 + i)
+        b = gen.gaussian_source(dims, seed=200 + i)
+        lat = wd.Lattice(dims)
+        lat.set_gauge(U, recon=recon)
+        lats.append(lat)
+        bs.append(lat.pack(b))
+        xs.append(lat.new_field())
+        inputs.append((U, b))
+    return lats, kappas, bs, xs, inputs
+
+
+@pytest.mark.parametrize("inner,recon", [(1, 18), (2, 18), (1, 12)])
+def test_batched_matches_oracle(wd, inner, recon):
+    lats, kappas, bs, xs, inputs = make_batch(wd, recon)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=inner)
+    assert st == 0, res
+    for i, (lat, (U, b)) in enumerate(zip(lats, inputs)):
+        assert res[i]["status"] == 0 and res[i]["true_rel_resid"] <= 1e-10
+        x_ref, _ = oracle.cgnr(U, b, kappas[i], lat.dims, tol=1e-13)
+        assert oracle.rel_err(lat.unpack(xs[i]), x_ref) < 1e-9, i
+    # uneven work: the lattices needed different iteration counts
+    assert len({r["iters"] for r in res}) > 1
+
+
+def test_batched_same_as_single_solves(wd):
+    """A lattice solved in the batch converges like the same lattice solved alone."""
+    lats, kappas, bs, xs, inputs = make_batch(wd)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 0
+    for i in (0, 4):
+        x1 = lats[i].new_field()
+        r1, st1 = lats[i].cg(kappas[i], bs[i], x1, tol=1e-10, inner=1)
+        assert st1 == 0
+        assert oracle.rel_err(lats[i].unpack(xs[i]), lats[i].unpack(x1)) < 1e-9
+
+
+def test_batched_wait_timeout_is_reported(wd, monkeypatch):
+    """A wait that nothing ends runs out: every lattice gets WD_ERR_TIMEOUT, the context stays usable."""
+    lats, kappas, bs, xs, inputs = make_batch(wd)
+    monkeypatch.setenv("WD_BATCH_STALL_TEST", "1")
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 7 and all(r["status"] == 7 for r in res)
+    monkeypatch.delenv("WD_BATCH_STALL_TEST")
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 0
+
+
+def test_batched_argument_errors(wd):
+    lats, kappas, bs, xs, _ = make_batch(wd)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=0)
+    assert st == 1
+    lats[1].set_gauge(gen.haar_links(lats[1].dims, 3), recon=12)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 1
