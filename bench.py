@@ -236,7 +236,12 @@ def main():
                     help="time only the Dslash kernel on this lattice (profiling helper)")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--compare", action="store_true",
+                    help="c3: FP64 vs FP32 vs FP16-storage solves; c4: 12 sequential FP64 solves vs multi-RHS "
+                         "and block CG; c5: batched persistent solve vs one-at-a-time FP64 solves")
     args = ap.parse_args()
+    if args.workload == "c5" or (args.compare and args.impl == "wd"):
+        return compare(args)
     w = WORKLOADS[args.workload]
     if args.dslash_only:
         return dslash_only(args)
@@ -404,6 +409,144 @@ def main():
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def _timed_solves(torch, fn, reps):
+    """Median device time (CUDA events) of `fn` over `reps` runs after one warm-up."""
+    fn()
+    ts = []
+    out = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), out
+
+
+def compare(args):
+    """Solver comparisons on one GPU (one JSON line with a `compare` object)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1810_04201_gb300 import gen, wd
+    reps = max(1, min(args.steps, 3))
+    line = {"workload": args.workload, "compare": {}}
+    if args.workload == "c5":
+        shapes, kappas, seeds = gen.batch_workload(64)
+        lats, bs, xs = [], [], []
+        for dims, seed in zip(shapes, seeds):
+            lat = wd.Lattice(dims)
+            lat.set_gauge(gen.haar_links(dims, seed), recon=args.recon)
+            lats.append(lat)
+            bs.append(lat.pack(gen.gaussian_source(dims, seed)))
+            xs.append(lat.new_field())
+        V = sum(l.V for l in lats)
+
+        def batched():
+            for x in xs:
+                x.zero_()
+            return wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=wd.WD_F32)
+
+        ms_b, (res_b, st_b) = _timed_solves(torch, batched, reps)
+        xb = [l.unpack(x) for l, x in zip(lats, xs)]
+        ys = [l.new_field() for l in lats]
+
+        def one_by_one():
+            out = []
+            for l, k, b, y in zip(lats, kappas, bs, ys):
+                y.zero_()
+                out.append(l.cg(k, b, y, tol=1e-10)[0][0])
+            return out
+
+        ms_s, res_s = _timed_solves(torch, one_by_one, reps)
+        err = max(oracle.rel_err(a, l.unpack(y)) for a, l, y in zip(xb, lats, ys))
+        line["compare"] = {
+            "lattices": 64, "total_sites": V, "shapes": sorted(set("x".join(map(str, d)) for d in shapes)),
+            "batched_mixed_f32": {"ms": round(ms_b, 3), "solves_per_s": round(64e3 / ms_b, 1),
+                                  "per_solve_latency_ms": round(ms_b, 3), "status": st_b,
+                                  "max_true_rel_resid": max(r["true_rel_resid"] for r in res_b),
+                                  "iters_min_max": [min(r["iters"] for r in res_b), max(r["iters"] for r in res_b)],
+                                  "gpu_launches": 1},
+            "one_at_a_time_f64": {"ms": round(ms_s, 3), "solves_per_s": round(64e3 / ms_s, 1),
+                                  "per_solve_latency_ms": round(ms_s / 64, 3),
+                                  "max_true_rel_resid": max(r["true_rel_resid"] for r in res_s)},
+            "speedup_batched_vs_f64": round(ms_s / ms_b, 3),
+            "max_rel_diff_batched_vs_f64_solutions": err,
+            "note": "per-solve latency of the batched launch = time until all 64 solutions are ready"}
+        print(json.dumps(line))
+        return
+    w = WORKLOADS[args.workload]
+    U, b = make_inputs(w, 0)
+    dims = w["dims"]
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=args.recon)
+    V = lat.V
+    if args.workload in ("c1", "c2", "c3"):
+        fb = lat.pack(b)
+        variants = {"f64": wd.WD_F64, "f32": wd.WD_F32, "f16": wd.WD_F16}
+        sols = {}
+        for name, inner in variants.items():
+            fx = lat.new_field()
+
+            def solve():
+                fx.zero_()
+                return lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=inner, raise_on_fail=False)
+
+            ms, (res, st) = _timed_solves(torch, solve, reps)
+            r = res[0]
+            x = lat.unpack(fx)
+            sols[name] = x
+            # the oracle's own operator on the GPU solution: ||b - D x|| / ||b||
+            t0 = time.perf_counter()
+            ores = oracle.rel_err(oracle.apply_D(U, x, w["kappa"], dims), b)
+            line["compare"][name] = {"ms": round(ms, 3), "iters": r["iters"], "reliable_updates": r["reliable_updates"],
+                                     "status": st, "true_rel_resid_normal": r["true_rel_resid"],
+                                     "true_rel_resid_b": r["true_rel_resid_b"], "oracle_rel_resid_b": ores,
+                                     "oracle_check_s": round(time.perf_counter() - t0, 2),
+                                     "gflops": round((2 * r["iters"] + 4 + 2 * r["reliable_updates"]) * 1320 * V
+                                                     / ms / 1e6, 1)}
+        for name in ("f32", "f16"):
+            line["compare"][name]["rel_diff_vs_f64_solution"] = oracle.rel_err(sols[name], sols["f64"])
+            line["compare"][name]["speedup_vs_f64"] = round(line["compare"]["f64"]["ms"] / line["compare"][name]["ms"], 3)
+    else:  # c4: 12 point sources
+        B = b
+        fb = lat.pack(B)
+        fbs = [lat.pack(B[k]) for k in range(12)]
+        fys = [lat.new_field() for _ in range(12)]
+
+        def seq():
+            res = []
+            for k in range(12):
+                fys[k].zero_()
+                res.append(lat.cg(w["kappa"], fbs[k], fys[k], tol=1e-10)[0][0])
+            return res
+
+        ms, res = _timed_solves(torch, seq, reps)
+        Xs = np.stack([lat.unpack(f) for f in fys])
+        line["compare"]["sequential_f64"] = {"ms": round(ms, 3), "iters_max": max(r["iters"] for r in res),
+                                            "max_true_rel_resid": max(r["true_rel_resid"] for r in res)}
+        for name, inner, block in (("multi_rhs_f64", wd.WD_F64, 0), ("multi_rhs_f32", wd.WD_F32, 0),
+                                   ("block_cg_f64", wd.WD_F64, 1)):
+            fx = lat.new_field(nrhs=12)
+
+            def solve():
+                fx.zero_()
+                return lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=inner, nrhs=12, block=block, raise_on_fail=False)
+
+            ms2, (res2, st2) = _timed_solves(torch, solve, reps)
+            X = lat.unpack(fx, nrhs=12, squeeze=False)
+            line["compare"][name] = {"ms": round(ms2, 3), "status": st2, "iters_max": max(r["iters"] for r in res2),
+                                     "max_true_rel_resid": max(r["true_rel_resid"] for r in res2),
+                                     "speedup_vs_sequential_f64": round(ms / ms2, 3),
+                                     "max_rel_diff_vs_sequential": max(oracle.rel_err(X[k], Xs[k]) for k in range(12))}
+    line["config"] = config_of(args, w)
+    print(json.dumps(line))
 
 
 def dslash_only(args):

@@ -254,6 +254,19 @@ def test_cgnr_matches_dense_lu_4x4():
     assert oracle.rel_err(x, xd) < 1e-9
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 2, 4), (4, 4, 2, 2)])
+def test_cg_within_chebyshev_bound(dims):
+    """CG on D^dag D reaches |r_k|/|r_0| <= eps within ln(2 sqrt(K)/eps) / ln((sqrt(K)+1)/(sqrt(K)-1))
+    iterations, K = cond(D^dag D) = (s_max / s_min)^2 from LAPACK's SVD of the assembled D."""
+    U = gen.haar_links(dims, seed=21)
+    b = gen.gaussian_source(dims, seed=22)
+    _, info = oracle.cgnr(U, b, 0.12, dims, tol=1e-12)
+    sv = np.linalg.svd(oracle.dense_matrix(U, 0.12, dims), compute_uv=False)
+    rk = sv[0] / sv[-1]
+    bound = np.log(2 * rk / 1e-12) / np.log((rk + 1) / (rk - 1))
+    assert info["converged"] and info["iters"] <= np.ceil(bound)
+
+
 def test_cgne_equals_cgnr():
     dims = (4, 2, 4, 4)
     U = gen.haar_links(dims, seed=31)
