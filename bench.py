@@ -40,10 +40,10 @@ if ROOT not in sys.path:
 FLOP_PER_SITE = 1320
 # Algorithmic bytes per site of one Dslash (each input field read once, output
 # written once): spinor in + links + spinor out.
-SPINOR_BYTES = {"f64": 192, "f32": 96, "f16": 52}
+SPINOR_BYTES = {"f64": 192, "f32": 96, "f16": 52, "df32": 192}
 LINK_BYTES = {("f64", 18): 576, ("f64", 12): 384, ("f32", 18): 288, ("f32", 12): 192, ("f16", 18): 144,
-              ("f16", 12): 96}
-PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
+              ("f16", 12): 96, ("df32", 18): 576, ("df32", 12): 384}
+PREC_ID = {"f64": 0, "f32": 1, "f16": 2, "df32": 3}
 WORKLOADS = {
     "c1": dict(dims=(4, 4, 4, 4), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=1),
     "c2": dict(dims=(16, 16, 16, 16), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=2),
@@ -227,14 +227,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wd", choices=["wd", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5"])
+    ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--recon", type=int, default=18, choices=[18, 12])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--sweep", action="store_true", help="also time the Dslash at 8^4, 12^4, 16^4, 24^4")
     ap.add_argument("--dslash-only", default=None, metavar="LX,LY,LZ,LT",
                     help="time only the Dslash kernel on this lattice (profiling helper)")
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--compare", action="store_true",
                     help="c3: FP64 vs FP32 vs FP16-storage solves; c4: 12 sequential FP64 solves vs multi-RHS "
@@ -489,7 +490,7 @@ def compare(args):
     V = lat.V
     if args.workload in ("c1", "c2", "c3"):
         fb = lat.pack(b)
-        variants = {"f64": wd.WD_F64, "f32": wd.WD_F32, "f16": wd.WD_F16}
+        variants = {"f64": wd.WD_F64, "f32": wd.WD_F32, "f16": wd.WD_F16, "df32": wd.WD_DF32}
         sols = {}
         for name, inner in variants.items():
             fx = lat.new_field()
@@ -511,7 +512,7 @@ def compare(args):
                                      "oracle_check_s": round(time.perf_counter() - t0, 2),
                                      "gflops": round((2 * r["iters"] + 4 + 2 * r["reliable_updates"]) * 1320 * V
                                                      / ms / 1e6, 1)}
-        for name in ("f32", "f16"):
+        for name in ("f32", "f16", "df32"):
             line["compare"][name]["rel_diff_vs_f64_solution"] = oracle.rel_err(sols[name], sols["f64"])
             line["compare"][name]["speedup_vs_f64"] = round(line["compare"]["f64"]["ms"] / line["compare"][name]["ms"], 3)
     else:  # c4: 12 point sources
@@ -532,6 +533,7 @@ def compare(args):
         line["compare"]["sequential_f64"] = {"ms": round(ms, 3), "iters_max": max(r["iters"] for r in res),
                                             "max_true_rel_resid": max(r["true_rel_resid"] for r in res)}
         for name, inner, block in (("multi_rhs_f64", wd.WD_F64, 0), ("multi_rhs_f32", wd.WD_F32, 0),
+                                   ("multi_rhs_f16", wd.WD_F16, 0), ("multi_rhs_df32", wd.WD_DF32, 0),
                                    ("block_cg_f64", wd.WD_F64, 1)):
             fx = lat.new_field(nrhs=12)
 

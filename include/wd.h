@@ -31,6 +31,7 @@
  *   WD_F32: 6 arrays of Vs float4 (two complex64 components each);
  *   WD_F16: 3 arrays of Vs x 16 B (four half2 components each), then Vs floats
  *           holding the per-site scale (the component of largest magnitude);
+ *   WD_DF32: 12 arrays of Vs float4 (re.hi, re.lo, im.hi, im.lo);
  * where Vs is V rounded up to a multiple of 64.  Right-hand sides follow each
  * other at a stride of wd_field_bytes(ctx, prec, 1).  Fields must be 256-byte
  * aligned (torch and cudaMalloc allocations are).
@@ -70,7 +71,16 @@ typedef enum wd_status {
     WD_ERR_STATE = 8          /* call out of order (e.g. no gauge field set) */
 } wd_status;
 
-typedef enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2 } wd_prec;
+/* Storage and arithmetic precision of a field and of the operator applied to it.
+ *   WD_F64   IEEE double.
+ *   WD_F32   IEEE single.
+ *   WD_F16   half-precision storage with a per-site FP32 scale, FP32 arithmetic.
+ *   WD_DF32  double-FP32: every real is the unevaluated sum of two floats (48-bit
+ *            significand), stored in the same 16 bytes per complex number as
+ *            WD_F64 and computed on the FP32 pipes with error-free transformations
+ *            (Knuth TwoSum, FMA TwoProduct).  The exponent range is that of FP32.
+ *            The operator matches the FP64 definition to about 1e-14 relative. */
+typedef enum wd_prec { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_DF32 = 3 } wd_prec;
 
 typedef struct wd_ctx wd_ctx;
 
@@ -132,12 +142,14 @@ wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, voi
 /* Solver parameters.
  *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side)
  *   max_iter   iteration limit
- *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16: mixed precision -- the Dslash
- *              and the inner iteration in FP32 (or FP16 storage with FP32 arithmetic),
- *              with FP64 reliable updates r = D^dag(b - D x) and the solution
- *              accumulated in FP64
+ *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16 / WD_DF32: mixed precision --
+ *              the Dslash and the inner iteration in FP32 (or FP16 storage with FP32
+ *              arithmetic, or double-FP32), with FP64 reliable updates
+ *              r = D^dag(b - D x) and the solution accumulated in FP64
  *   delta      reliable-update trigger: an update runs when the iterated residual
- *              drops below delta times its maximum since the last update (0 = 0.1)
+ *              drops below delta times its maximum since the last update (0 = the
+ *              default of the inner precision: 1e-2 for WD_F16, 1e-3 for WD_F32,
+ *              1e-6 for WD_DF32)
  *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
  *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
  *              1: block CG (one Krylov space for all right-hand sides, FP64 only)

@@ -59,10 +59,12 @@ wd_status gauge_get(wd_ctx *c, Prec p, const void **out) {
         if (c->recon == 12) {
             if (p == F64) gauge_pack<F64, 12>(c->gauge_canon, d, c->g, dir, c->stream);
             else if (p == F32) gauge_pack<F32, 12>(c->gauge_canon, d, c->g, dir, c->stream);
+            else if (p == DF32) gauge_pack<DF32, 12>(c->gauge_canon, d, c->g, dir, c->stream);
             else gauge_pack<F16, 12>(c->gauge_canon, d, c->g, dir, c->stream);
         } else {
             if (p == F64) gauge_pack<F64, 18>(c->gauge_canon, d, c->g, dir, c->stream);
             else if (p == F32) gauge_pack<F32, 18>(c->gauge_canon, d, c->g, dir, c->stream);
+            else if (p == DF32) gauge_pack<DF32, 18>(c->gauge_canon, d, c->g, dir, c->stream);
             else gauge_pack<F16, 18>(c->gauge_canon, d, c->g, dir, c->stream);
         }
         WD_CUDA(c, cudaGetLastError());
@@ -87,12 +89,12 @@ DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs) {
 wd_ctx::~wd_ctx() {
     for (auto &g : graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
     for (auto &w : ws) cudaFree(w.second);
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < kNumPrec; ++p)
         if (gauge[p]) cudaFree(gauge[p]);
     if (gauge_canon) cudaFree(gauge_canon);
 }
 
-static bool bad_prec(int p) { return p < 0 || p > 2; }
+static bool bad_prec(int p) { return p < 0 || p >= kNumPrec; }
 
 extern "C" {
 
@@ -161,7 +163,7 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     if (recon != 18 && recon != 12) return fail(c, WD_ERR_ARG, "wd_set_gauge: recon must be 18 or 12");
     const size_t bytes = (size_t)4 * c->g.V * 9 * 16;
     WD_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < kNumPrec; ++p)
         if (c->gauge[p]) {
             cudaFree(c->gauge[p]);
             c->gauge[p] = nullptr;
@@ -214,6 +216,7 @@ wd_status wd_pack(wd_ctx *c, const double *canon, int on_device, void *field, wd
     dim3 grid((c->g.V + 127) / 128, nrhs);
     if (prec == WD_F64) k_pack<F64><<<grid, 128, 0, c->stream>>>(v);
     else if (prec == WD_F32) k_pack<F32><<<grid, 128, 0, c->stream>>>(v);
+    else if (prec == WD_DF32) k_pack<DF32><<<grid, 128, 0, c->stream>>>(v);
     else k_pack<F16><<<grid, 128, 0, c->stream>>>(v);
     WD_CUDA(c, cudaGetLastError());
     c->launches += 1;
@@ -238,6 +241,7 @@ wd_status wd_unpack(wd_ctx *c, const void *field, wd_prec prec, int nrhs, double
     dim3 grid((c->g.V + 127) / 128, nrhs);
     if (prec == WD_F64) k_unpack<F64><<<grid, 128, 0, c->stream>>>(v);
     else if (prec == WD_F32) k_unpack<F32><<<grid, 128, 0, c->stream>>>(v);
+    else if (prec == WD_DF32) k_unpack<DF32><<<grid, 128, 0, c->stream>>>(v);
     else k_unpack<F16><<<grid, 128, 0, c->stream>>>(v);
     WD_CUDA(c, cudaGetLastError());
     c->launches += 1;

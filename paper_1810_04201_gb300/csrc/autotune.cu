@@ -18,7 +18,7 @@ extern "C" {
 
 wd_status wd_set_tiles(wd_ctx *c, wd_prec prec, int nrhs, int site_tile, int rhs_tile) {
     if (!c) return WD_ERR_ARG;
-    if ((int)prec < 0 || (int)prec > 2 || nrhs < 1 || nrhs > WD_MAX_RHS || rhs_tile < 1 || rhs_tile > nrhs ||
+    if ((int)prec < 0 || (int)prec >= kNumPrec || nrhs < 1 || nrhs > WD_MAX_RHS || rhs_tile < 1 || rhs_tile > nrhs ||
         (site_tile != 16 && site_tile != 32 && site_tile != 64 && site_tile != 128 && site_tile != 256) ||
         site_tile * rhs_tile > 256 || (site_tile * rhs_tile) % 32 != 0)
         return fail(c, WD_ERR_ARG, "wd_set_tiles: unsupported tile shape");
@@ -32,7 +32,7 @@ wd_status wd_set_tiles(wd_ctx *c, wd_prec prec, int nrhs, int site_tile, int rhs
 wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile) {
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
-    if ((int)prec < 0 || (int)prec > 2 || nrhs < 1 || nrhs > WD_MAX_RHS)
+    if ((int)prec < 0 || (int)prec >= kNumPrec || nrhs < 1 || nrhs > WD_MAX_RHS)
         return fail(c, WD_ERR_ARG, "wd_autotune: bad argument");
     const void *gauge;
     wd_status s = gauge_get(c, (Prec)prec, &gauge);

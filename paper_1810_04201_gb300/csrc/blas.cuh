@@ -140,6 +140,12 @@ template <int P, int RECON> __global__ void k_gauge_pack(const double2 *canon, v
     if (P == F64) {
         double2 *d = reinterpret_cast<double2 *>(base) + s;
         for (int e = 0; e < n; ++e) d[(size_t)e * Vs] = u[e];
+    } else if (P == DF32) {
+        float4 *d = reinterpret_cast<float4 *>(base) + s;
+        for (int e = 0; e < n; ++e) {
+            const df re(u[e].x), im(u[e].y);
+            d[(size_t)e * Vs] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
     } else if (P == F32) {
         float4 *d = reinterpret_cast<float4 *>(base) + s;
         const int n4 = n / 2;

@@ -171,6 +171,7 @@ static cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, c
     switch (pl.inner) {
     case F64: return build_graph<RECON, F64>(c, pl, f, g64, gin, exec, counts);
     case F32: return build_graph<RECON, F32>(c, pl, f, g64, gin, exec, counts);
+    case DF32: return build_graph<RECON, DF32>(c, pl, f, g64, gin, exec, counts);
     default: return build_graph<RECON, F16>(c, pl, f, g64, gin, exec, counts);
     }
 }
@@ -180,6 +181,7 @@ static void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const v
     switch (pl.inner) {
     case F64: record_plan<RECON, F64>(c, pl, f, g64, gin, 0, 0, plan); break;
     case F32: record_plan<RECON, F32>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case DF32: record_plan<RECON, DF32>(c, pl, f, g64, gin, 0, 0, plan); break;
     default: record_plan<RECON, F16>(c, pl, f, g64, gin, 0, 0, plan); break;
     }
 }
@@ -226,7 +228,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (!b || !x || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve: null argument");
     const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;
     if (nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_cg_solve: nrhs above WD_MAX_RHS");
-    if (prm->inner_prec < 0 || prm->inner_prec > 2) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad inner_prec");
+    if (prm->inner_prec < 0 || prm->inner_prec >= kNumPrec) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad inner_prec");
     if (!(prm->tol > 0) || !std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad tol or kappa");
     if (b == x) return fail(c, WD_ERR_ARG, "wd_cg_solve: b and x must be distinct");
     if (prm->block) {
@@ -248,7 +250,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         if ((s = ws_get(c, n64[i], s64, p64[i])) != WD_OK) return s;
     if (inner != F64) {
         const size_t sin = spinor_bytes(inner, c->g.Vs) * nrhs;
-        std::string sfx = inner == F32 ? "32" : "16";
+        std::string sfx = inner == F32 ? "32" : inner == F16 ? "16" : "d32";
         if ((s = ws_get(c, "cg_rs" + sfx, sin, &f.rs)) != WD_OK) return s;
         if ((s = ws_get(c, "cg_ps" + sfx, sin, &f.ps)) != WD_OK) return s;
         if ((s = ws_get(c, "cg_ts" + sfx, sin, &f.ts)) != WD_OK) return s;
@@ -293,7 +295,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
 
     // per-RHS state
     std::vector<Scalars> h(nrhs);
-    const double delta = prm->delta > 0 ? prm->delta : 0.1;
+    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec);
     for (int r = 0; r < nrhs; ++r) {
         std::memset(&h[r], 0, sizeof(Scalars));
         h[r].tol2 = prm->tol * prm->tol;

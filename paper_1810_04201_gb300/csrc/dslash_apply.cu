@@ -23,6 +23,7 @@ cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, Ds
     switch (p) {
     case F64: return go_p<F64>(a, recon, dagger, t, st);
     case F32: return go_p<F32>(a, recon, dagger, t, st);
+    case DF32: return go_p<DF32>(a, recon, dagger, t, st);
     default: return go_p<F16>(a, recon, dagger, t, st);
     }
 }

@@ -18,10 +18,12 @@
 #include <map>
 
 #include "../../include/wd.h"
+#include "df32.cuh"
 
 namespace wd {
 
-enum Prec { F64 = 0, F32 = 1, F16 = 2 };
+enum Prec { F64 = 0, F32 = 1, F16 = 2, DF32 = 3 };
+constexpr int kNumPrec = 4;
 
 constexpr int kSiteAlign = 64;
 inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
@@ -57,13 +59,14 @@ struct Geom {
 // ------------------------------------------------------------------ field sizes
 inline size_t spinor_bytes(Prec p, int Vs) {
     switch (p) {
-    case F64: return (size_t)12 * Vs * 16;
+    case F64:
+    case DF32: return (size_t)12 * Vs * 16;
     case F32: return (size_t)6 * Vs * 16;
     default: return round_up((size_t)3 * Vs * 16 + (size_t)Vs * 4, 256);
     }
 }
 inline size_t link_dir_bytes(Prec p, int recon, int Vs) {
-    if (p == F64) return (size_t)(recon == 12 ? 6 : 9) * Vs * 16;
+    if (p == F64 || p == DF32) return (size_t)(recon == 12 ? 6 : 9) * Vs * 16;
     if (p == F32) return recon == 12 ? (size_t)3 * Vs * 16 : (size_t)4 * Vs * 16 + (size_t)Vs * 8;
     return recon == 12 ? (size_t)Vs * 16 + (size_t)Vs * 8 : (size_t)2 * Vs * 16 + (size_t)Vs * 4;
 }
@@ -72,6 +75,7 @@ inline size_t gauge_bytes(Prec p, int recon, int Vs) { return 4 * round_up(link_
 // ------------------------------------------------------------------ precision traits
 template <int P> struct Real { using T = float; };
 template <> struct Real<F64> { using T = double; };
+template <> struct Real<DF32> { using T = df; };
 
 // Global loads: the read-only path (ld.global.nc) for fields a launch only reads,
 // plain coherent loads (NC = false) for fields that other blocks of the same
@@ -121,6 +125,25 @@ template <> struct SpinorIO<F32> {
     }
 };
 
+// DF32: one float4 (re.hi, re.lo, im.hi, im.lo) per complex component, 12 arrays.
+template <> struct SpinorIO<DF32> {
+    using R = df;
+    template <bool NC = true>
+    static __device__ __forceinline__ void load(const void *base, int Vs, int s, C<R> (&v)[12]) {
+        const float4 *p = reinterpret_cast<const float4 *>(base) + s;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float4 t = ldx<NC>(p + (size_t)c * Vs);
+            v[c] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+        }
+    }
+    static __device__ __forceinline__ void store(void *base, int Vs, int s, const C<R> (&v)[12]) {
+        float4 *p = reinterpret_cast<float4 *>(base) + s;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[(size_t)c * Vs] = make_float4(v[c].re.hi, v[c].re.lo, v[c].im.hi, v[c].im.lo);
+    }
+};
+
 __device__ __forceinline__ float2 h2f(uint32_t u) {
     __half2 h = *reinterpret_cast<__half2 *>(&u);
     return __half22float2(h);
@@ -153,7 +176,10 @@ template <> struct SpinorIO<F16> {
         float m = 0.f;
 #pragma unroll
         for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf(v[c].re), fabsf(v[c].im)));
-        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        // sites whose largest component is below 1e-37 are stored as zero: the
+        // reciprocal of a smaller scale would overflow FP32
+        const float inv = m > 1e-37f ? 1.0f / m : 0.f;
+        if (!(m > 1e-37f)) m = 0.f;
         uint4 *p = reinterpret_cast<uint4 *>(base) + s;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -210,6 +236,20 @@ template <int RECON> struct LinkIO<F32, RECON> {
             float2 t = __ldg(q);
             u[8] = C<R>{t.x, t.y};
         }
+    }
+};
+
+template <int RECON> struct LinkIO<DF32, RECON> {
+    using R = df;
+    static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
+        const float4 *p = reinterpret_cast<const float4 *>(dir_base) + s;
+        constexpr int n = RECON == 12 ? 6 : 9;
+#pragma unroll
+        for (int e = 0; e < n; ++e) {
+            float4 t = __ldg(p + (size_t)e * Vs);
+            u[e] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+        }
+        if (RECON == 12) rebuild_row2(u);
     }
 };
 
@@ -328,6 +368,19 @@ __device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
     return mask == 1 ? sc[r].active != 0 : sc[r].do_update != 0;
 }
 
+// Default reliable-update threshold per inner precision: an FP64 update runs when
+// the iterated residual has dropped by this factor since the last one.  Low
+// precisions need frequent updates; FP64 updates are expensive on a part with a
+// thin FP64 pipe, so the threshold is as small as each precision allows.
+inline double default_delta(Prec p) {
+    switch (p) {
+    case F16: return 1e-2;
+    case F32: return 1e-3;
+    case DF32: return 1e-6;
+    default: return 0.1;
+    }
+}
+
 struct DslashTiles { int site_tile = 128; int rhs_tile = 1; };
 
 }  // namespace wd
@@ -339,7 +392,7 @@ struct wd_ctx {
     int device = 0;
     int recon = 18;
     bool has_gauge = false;
-    void *gauge[3] = {nullptr, nullptr, nullptr};    // per precision (at this->recon)
+    void *gauge[wd::kNumPrec] = {};                    // per precision (at this->recon)
     double *gauge_canon = nullptr;                     // FP64 canonical copy on device
     std::string last_error;
     long long launches = 0;

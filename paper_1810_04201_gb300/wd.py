@@ -17,8 +17,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libwd.so")
 
-WD_F64, WD_F32, WD_F16 = 0, 1, 2
-PRECS = {"f64": WD_F64, "f32": WD_F32, "f16": WD_F16}
+WD_F64, WD_F32, WD_F16, WD_DF32 = 0, 1, 2, 3
+PRECS = {"f64": WD_F64, "f32": WD_F32, "f16": WD_F16, "df32": WD_DF32}
 STATUS = {0: "WD_OK", 1: "WD_ERR_ARG", 2: "WD_ERR_CUDA", 3: "WD_ERR_OOM", 4: "WD_ERR_NOT_CONVERGED",
           5: "WD_ERR_BREAKDOWN", 6: "WD_ERR_NONFINITE", 7: "WD_ERR_TIMEOUT", 8: "WD_ERR_STATE"}
 MAX_RHS = 16
@@ -199,10 +199,10 @@ class Lattice:
 
     # ------------------------------------------------------------------ solvers
     @staticmethod
-    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1, block=0, rhs_tile=0):
+    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0):
         return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile)
 
-    def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1, block=0,
+    def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0,
            raise_on_fail=True):
         """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results."""
         p = self.params(tol, max_iter, inner, delta, nrhs, block)
@@ -213,7 +213,7 @@ class Lattice:
             self._check(st, "wd_cg_solve")
         return [r.as_dict() for r in res], st
 
-    def cg_canonical(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.1, nrhs=1,
+    def cg_canonical(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1,
                      raise_on_fail=True):
         """End-to-end solve on canonical host arrays (numpy complex128, pinned torch CPU tensors
         allowed) or device tensors; x is overwritten with the solution."""
@@ -239,7 +239,7 @@ class Lattice:
         self._check(self.lib.wd_set_tiles(self.ctx, prec, nrhs, site_tile, rhs_tile), "wd_set_tiles")
 
 
-def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32, delta=0.1):
+def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32, delta=0.0):
     """Solve many independent lattices in one persistent launch (wd_cg_solve_batched)."""
     lib = load_library()
     n = len(lattices)

@@ -28,7 +28,7 @@ def ref_solution(U, b, kappa, dims):
     return x, info
 
 
-@pytest.mark.parametrize("inner", [0, 1, 2])
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
 def test_cg_4x4(wd, inner):
     dims, kappa = (4, 4, 4, 4), 0.12
     U = gen.haar_links(dims, seed=1)
@@ -49,7 +49,7 @@ def test_cg_4x4(wd, inner):
         assert r["reliable_updates"] >= 1
 
 
-@pytest.mark.parametrize("inner", [0, 1, 2])
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
 @pytest.mark.parametrize("recon", [18, 12])
 def test_cg_odd_shapes(wd, inner, recon):
     dims, kappa = (6, 6, 6, 8), 0.124
@@ -78,7 +78,7 @@ def test_cg_dense_lu_2x4(wd):
     assert oracle.rel_err(lat.unpack(fx), xd) < 1e-10
 
 
-@pytest.mark.parametrize("inner", [0, 1])
+@pytest.mark.parametrize("inner", [0, 1, 2, 3])
 def test_cg_multi_rhs_point_sources(wd, inner):
     dims, kappa = (4, 4, 4, 8), 0.12
     U = gen.haar_links(dims, seed=7)

@@ -6,7 +6,9 @@ Tolerances (relative per-field 2-norm):
   * FP32: 2e-6 (single-precision storage of inputs and links, about 40 rounding
     steps per output component at 6e-8 each);
   * FP16 storage: 4e-3 (half-precision storage, 2^-11 relative to the per-site
-    scale, FP32 arithmetic).
+    scale, FP32 arithmetic);
+  * DF32 (pairs of floats, 48-bit significand): the FP64 tolerance, 1e-13 (inputs
+    rounded to 2^-49 relative, about 40 operations per output at ~2^-47 each).
 """
 import numpy as np
 import pytest
@@ -16,7 +18,7 @@ from paper_1810_04201_gb300 import gen
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3}
+TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3, 3: 1e-13}
 KAPPA = 0.12
 
 
@@ -32,7 +34,7 @@ SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 6, 6, 8), (3, 5, 4, 6), (8, 8, 8, 12),
 
 
 @pytest.mark.parametrize("dims", SHAPES)
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("recon", [18, 12])
 def test_dslash_parity(wd, dims, prec, recon):
     U = gen.haar_links(dims, seed=2)
@@ -48,7 +50,7 @@ def test_dslash_parity(wd, dims, prec, recon):
         assert oracle.rel_err(got, ref) < TOL[prec], (dagger, oracle.rel_err(got, ref))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_periodic_time_and_paper_sign(wd, prec):
     dims = (4, 4, 2, 6)
     U = gen.haar_links(dims, seed=8)
@@ -91,6 +93,15 @@ def test_normal_op_parity(wd):
     assert oracle.rel_err(lat.unpack(o), oracle.apply_normal(U, psi, KAPPA, dims)) < 1e-13
 
 
+def test_df32_pack_roundtrip_and_range(wd):
+    """DF32 keeps 48 significand bits: a pack/unpack round trip is exact to 2^-48 relative."""
+    dims = (4, 4, 4, 4)
+    psi = gen.gaussian_source(dims, seed=2) * np.exp(np.linspace(-20, 20, 256 * 12)).reshape(256, 4, 3)
+    lat = wd.Lattice(dims)
+    back = lat.unpack(lat.pack(psi, 3), 3)
+    assert np.max(np.abs(back - psi) / np.abs(psi)) < 2.0 ** -47
+
+
 def test_pack_unpack_roundtrip_bit_exact(wd):
     dims = (3, 5, 4, 6)
     psi = gen.gaussian_source(dims, seed=1, nrhs=2)
@@ -109,7 +120,7 @@ def test_full_size_sampled(wd, dims):
     V = int(np.prod(dims))
     sites = np.unique(np.concatenate([np.arange(64), V - 1 - np.arange(64),
                                       gen.uniform(3, 9, 0, 256).__mul__(V).astype(np.int64)]))
-    for prec in (0, 1):
+    for prec in (0, 1, 3):
         f = lat.pack(psi, prec)
         o = lat.new_field(prec)
         for dagger in (False, True):
