@@ -145,6 +145,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time: every rank gets the maximum of x over the job."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(flops_per_rank_step: float, step_ms: float, world: int) -> float:
+    """Whole-job GFLOP/s: every rank solves its own lattice (replicas), timed by the slowest."""
+    return world * flops_per_rank_step / (step_ms * 1e-3) / 1e9
+
+
 def make_inputs(w, rank):
     from paper_1810_04201_gb300 import gen
     seed = w["seed"] + 1000 * rank
@@ -364,12 +379,8 @@ def main():
                "ms_per_step": round(e2e_s * 1e3, 3), "gpu_launches_per_step": int(launches_e2e)}
 
     # max over ranks
-    step_ms = total_ms / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * flops_step / (step_ms * 1e-3) / 1e9
+    step_ms = max_over_ranks(total_ms / args.steps, dist, "cuda")
+    value = job_throughput(flops_step, step_ms, world)
 
     if rank != 0:
         if dist:

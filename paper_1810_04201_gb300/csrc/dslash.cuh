@@ -83,6 +83,30 @@ __device__ __forceinline__ void accumulate(C<R> (&acc)[12], const C<R> (&w)[6]) 
     }
 }
 
+template <int P> struct HasScale { static constexpr bool value = false; };
+template <> struct HasScale<F16> { static constexpr bool value = true; };
+
+// w = scale * U h (forward) or scale * U^dag h (backward), two colour vectors
+template <bool ADJ, class R>
+__device__ __forceinline__ void su3_mult_scaled(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], R scale) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C<R> s;
+            if (!ADJ) {
+                s = cmul(u[3 * a + 0], h[3 * sp + 0]);
+                s = cadd(s, cmul(u[3 * a + 1], h[3 * sp + 1]));
+                s = cadd(s, cmul(u[3 * a + 2], h[3 * sp + 2]));
+            } else {
+                s = cmulc(u[0 + a], h[3 * sp + 0]);
+                s = cadd(s, cmulc(u[3 + a], h[3 * sp + 1]));
+                s = cadd(s, cmulc(u[6 + a], h[3 * sp + 2]));
+            }
+            w[3 * sp + a] = cscale(scale, s);
+        }
+}
+
 // w = U h (forward) or U^dag h (backward), two colour vectors; optional sign flip
 template <bool ADJ, class R>
 __device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], bool flip) {
@@ -112,20 +136,37 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     const int L = g.L[MU], st = g.stride[MU];
     {
         const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+        const bool flip = MU == 3 && g.antiperiodic && c == L - 1;
         C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
-        project<MU, SF>(p, h);
-        LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
-        su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
+        if constexpr (HasScale<P>::value) {
+            // FP16: project the raw values, apply site scale and boundary sign once to U h
+            const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sf, p);
+            project<MU, SF>(p, h);
+            LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
+            su3_mult_scaled<false>(u, h, w, flip ? -scale : scale);
+        } else {
+            SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
+            project<MU, SF>(p, h);
+            LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
+            su3_mult<false>(u, h, w, flip);
+        }
         accumulate<MU, SF>(acc, w);
     }
     {
         const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+        const bool flip = MU == 3 && g.antiperiodic && c == 0;
         C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
-        project<MU, -SF>(p, h);
-        LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
-        su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+        if constexpr (HasScale<P>::value) {
+            const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sb, p);
+            project<MU, -SF>(p, h);
+            LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
+            su3_mult_scaled<true>(u, h, w, flip ? -scale : scale);
+        } else {
+            SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
+            project<MU, -SF>(p, h);
+            LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
+            su3_mult<true>(u, h, w, flip);
+        }
         accumulate<MU, -SF>(acc, w);
     }
 }
@@ -155,8 +196,16 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
 // handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
 // one site; Ep::finish runs once per thread after the loop (block and grid
 // reductions, solver scalars).
+// Minimum resident 256-thread blocks per SM the compiler must allow for: the
+// DF32 kernel is issue-bound and needs more resident warps than its natural
+// register count (about 170) would give.
+#ifndef WD_DF32_MIN_BLOCKS
+#define WD_DF32_MIN_BLOCKS 1
+#endif
+template <int P> constexpr int dslash_min_blocks() { return P == DF32 ? WD_DF32_MIN_BLOCKS : 1; }
+
 template <int P, int RECON, bool DAG, class Ep>
-__global__ void __launch_bounds__(256) dslash_kernel(DslashArgs a) {
+__global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(DslashArgs a) {
     using R = typename Real<P>::T;
     if (a.run_flag && *a.run_flag == 0) return;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
