@@ -96,12 +96,12 @@ __device__ __forceinline__ void su3_mult_scaled(const C<R> (&u)[9], const C<R> (
             C<R> s;
             if (!ADJ) {
                 s = cmul(u[3 * a + 0], h[3 * sp + 0]);
-                s = cadd(s, cmul(u[3 * a + 1], h[3 * sp + 1]));
-                s = cadd(s, cmul(u[3 * a + 2], h[3 * sp + 2]));
+                s = cmac(s, u[3 * a + 1], h[3 * sp + 1]);
+                s = cmac(s, u[3 * a + 2], h[3 * sp + 2]);
             } else {
                 s = cmulc(u[0 + a], h[3 * sp + 0]);
-                s = cadd(s, cmulc(u[3 + a], h[3 * sp + 1]));
-                s = cadd(s, cmulc(u[6 + a], h[3 * sp + 2]));
+                s = cmacc(s, u[3 + a], h[3 * sp + 1]);
+                s = cmacc(s, u[6 + a], h[3 * sp + 2]);
             }
             w[3 * sp + a] = cscale(scale, s);
         }
@@ -117,12 +117,12 @@ __device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6],
             C<R> s;
             if (!ADJ) {
                 s = cmul(u[3 * a + 0], h[3 * sp + 0]);
-                s = cadd(s, cmul(u[3 * a + 1], h[3 * sp + 1]));
-                s = cadd(s, cmul(u[3 * a + 2], h[3 * sp + 2]));
+                s = cmac(s, u[3 * a + 1], h[3 * sp + 1]);
+                s = cmac(s, u[3 * a + 2], h[3 * sp + 2]);
             } else {
                 s = cmulc(u[0 + a], h[3 * sp + 0]);
-                s = cadd(s, cmulc(u[3 + a], h[3 * sp + 1]));
-                s = cadd(s, cmulc(u[6 + a], h[3 * sp + 2]));
+                s = cmacc(s, u[3 + a], h[3 * sp + 1]);
+                s = cmacc(s, u[6 + a], h[3 * sp + 2]);
             }
             w[3 * sp + a] = flip ? cneg(s) : s;
         }
@@ -136,37 +136,48 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     const int L = g.L[MU], st = g.stride[MU];
     {
         const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
-        const bool flip = MU == 3 && g.antiperiodic && c == L - 1;
         C<R> p[12], h[6], w[6], u[9];
-        if constexpr (HasScale<P>::value) {
-            // FP16: project the raw values, apply site scale and boundary sign once to U h
-            const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sf, p);
-            project<MU, SF>(p, h);
-            LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
-            su3_mult_scaled<false>(u, h, w, flip ? -scale : scale);
-        } else {
-            SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
-            project<MU, SF>(p, h);
-            LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
-            su3_mult<false>(u, h, w, flip);
-        }
+        SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
+        project<MU, SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
+        su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
         accumulate<MU, SF>(acc, w);
     }
     {
         const int sb = (c == 0) ? s + (L - 1) * st : s - st;
-        const bool flip = MU == 3 && g.antiperiodic && c == 0;
         C<R> p[12], h[6], w[6], u[9];
-        if constexpr (HasScale<P>::value) {
-            const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sb, p);
-            project<MU, -SF>(p, h);
-            LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
-            su3_mult_scaled<true>(u, h, w, flip ? -scale : scale);
-        } else {
-            SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
-            project<MU, -SF>(p, h);
-            LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
-            su3_mult<true>(u, h, w, flip);
-        }
+        SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
+        project<MU, -SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
+        su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+        accumulate<MU, -SF>(acc, w);
+    }
+}
+
+// FP16: project the raw half values, then apply the site scale and the boundary
+// sign once, to U h (12 multiplies instead of 24 per neighbour).
+template <int P, int RECON, bool DAG, int MU, bool NC = true>
+__device__ __forceinline__ void hop_dir_scaled(const Geom &g, const void *in, const char *gdir, int s, int c,
+                                               C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+    constexpr int SF = DAG ? +1 : -1;
+    const int L = g.L[MU], st = g.stride[MU];
+    {
+        const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+        C<R> p[12], h[6], w[6], u[9];
+        const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sf, p);
+        project<MU, SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
+        su3_mult_scaled<false>(u, h, w, (MU == 3 && g.antiperiodic && c == L - 1) ? -scale : scale);
+        accumulate<MU, SF>(acc, w);
+    }
+    {
+        const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+        C<R> p[12], h[6], w[6], u[9];
+        const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sb, p);
+        project<MU, -SF>(p, h);
+        LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
+        su3_mult_scaled<true>(u, h, w, (MU == 3 && g.antiperiodic && c == 0) ? -scale : scale);
         accumulate<MU, -SF>(acc, w);
     }
 }
@@ -184,10 +195,17 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
     const int z = rem % g.L[2];
     const int t = rem / g.L[2];
     const char *gb = reinterpret_cast<const char *>(gauge);
-    hop_dir<P, RECON, DAG, 0, NC>(g, in, gb, s, x, acc);
-    hop_dir<P, RECON, DAG, 1, NC>(g, in, gb + gdir_bytes, s, y, acc);
-    hop_dir<P, RECON, DAG, 2, NC>(g, in, gb + 2 * gdir_bytes, s, z, acc);
-    hop_dir<P, RECON, DAG, 3, NC>(g, in, gb + 3 * gdir_bytes, s, t, acc);
+    if constexpr (HasScale<P>::value) {
+        hop_dir_scaled<P, RECON, DAG, 0, NC>(g, in, gb, s, x, acc);
+        hop_dir_scaled<P, RECON, DAG, 1, NC>(g, in, gb + gdir_bytes, s, y, acc);
+        hop_dir_scaled<P, RECON, DAG, 2, NC>(g, in, gb + 2 * gdir_bytes, s, z, acc);
+        hop_dir_scaled<P, RECON, DAG, 3, NC>(g, in, gb + 3 * gdir_bytes, s, t, acc);
+    } else {
+        hop_dir<P, RECON, DAG, 0, NC>(g, in, gb, s, x, acc);
+        hop_dir<P, RECON, DAG, 1, NC>(g, in, gb + gdir_bytes, s, y, acc);
+        hop_dir<P, RECON, DAG, 2, NC>(g, in, gb + 2 * gdir_bytes, s, z, acc);
+        hop_dir<P, RECON, DAG, 3, NC>(g, in, gb + 3 * gdir_bytes, s, t, acc);
+    }
 }
 
 // Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks
@@ -196,13 +214,86 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
 // handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
 // one site; Ep::finish runs once per thread after the loop (block and grid
 // reductions, solver scalars).
-// Minimum resident 256-thread blocks per SM the compiler must allow for: the
-// DF32 kernel is issue-bound and needs more resident warps than its natural
-// register count (about 170) would give.
-#ifndef WD_DF32_MIN_BLOCKS
-#define WD_DF32_MIN_BLOCKS 1
-#endif
-template <int P> constexpr int dslash_min_blocks() { return P == DF32 ? WD_DF32_MIN_BLOCKS : 1; }
+// The same hopping sum as a rolled loop over the 8 hops (direction mu = hop / 2,
+// forward when hop is even).  The code of one hop is reused 8 times, so the
+// instruction footprint stays small; used for DF32, whose fully unrolled form is
+// large enough to miss in the instruction cache.
+template <class R>
+__device__ __forceinline__ void project_rt(int mu, int sgn, const C<R> (&p)[12], C<R> (&h)[6]) {
+    if (sgn > 0) {
+        switch (mu) {
+        case 0: project<0, 1>(p, h); break;
+        case 1: project<1, 1>(p, h); break;
+        case 2: project<2, 1>(p, h); break;
+        default: project<3, 1>(p, h); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: project<0, -1>(p, h); break;
+        case 1: project<1, -1>(p, h); break;
+        case 2: project<2, -1>(p, h); break;
+        default: project<3, -1>(p, h); break;
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void accumulate_rt(int mu, int sgn, C<R> (&acc)[12], const C<R> (&w)[6]) {
+    if (sgn > 0) {
+        switch (mu) {
+        case 0: accumulate<0, 1>(acc, w); break;
+        case 1: accumulate<1, 1>(acc, w); break;
+        case 2: accumulate<2, 1>(acc, w); break;
+        default: accumulate<3, 1>(acc, w); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: accumulate<0, -1>(acc, w); break;
+        case 1: accumulate<1, -1>(acc, w); break;
+        case 2: accumulate<2, -1>(acc, w); break;
+        default: accumulate<3, -1>(acc, w); break;
+        }
+    }
+}
+
+template <int P, int RECON, bool DAG, bool NC = true>
+__device__ __forceinline__ void hopping_rolled(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes,
+                                               int s, C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = C<R>{R(0), R(0)};
+    const char *gb = reinterpret_cast<const char *>(gauge);
+#pragma unroll 1
+    for (int hop = 0; hop < 8; ++hop) {
+        const int mu = hop >> 1;
+        const bool fwd = (hop & 1) == 0;
+        const int L = g.L[mu], st = g.stride[mu];
+        const int cm = (s / st) % L;
+        int sn;
+        bool flip;
+        if (fwd) {
+            sn = (cm == L - 1) ? s - (L - 1) * st : s + st;
+            flip = mu == 3 && g.antiperiodic && cm == L - 1;
+        } else {
+            sn = (cm == 0) ? s + (L - 1) * st : s - st;
+            flip = mu == 3 && g.antiperiodic && cm == 0;
+        }
+        // forward hop: projector 1 - gamma (D) or 1 + gamma (D^dag); backward: the opposite
+        const int sgn = fwd == DAG ? 1 : -1;
+        C<R> p[12], h[6], w[6], u[9];
+        SpinorIO<P>::template load<NC>(in, g.Vs, sn, p);
+        project_rt(mu, sgn, p, h);
+        LinkIO<P, RECON>::load(gb + (size_t)mu * gdir_bytes, g.Vs, fwd ? s : sn, u);
+        if (fwd) su3_mult<false>(u, h, w, flip);
+        else su3_mult<true>(u, h, w, flip);
+        accumulate_rt(mu, sgn, acc, w);
+    }
+}
+
+// Register budget: the FP32 and FP16 kernels are memory-bound and want many
+// resident warps, so they are held to 3 blocks of 256 threads per SM (at most 85
+// registers); FP64 and DF32 are arithmetic-bound and keep the compiler's choice.
+template <int P> constexpr int dslash_min_blocks() { return (P == F32 || P == F16) ? 3 : 0; }
 
 template <int P, int RECON, bool DAG, class Ep>
 __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(DslashArgs a) {
@@ -216,7 +307,8 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
         const int s = s0 + threadIdx.x;
         if (row && s < a.g.V) {
             C<R> acc[12];
-            hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            if constexpr (P == DF32) hopping_rolled<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
             Ep::template site<P>(a, s, r, in, acc, st);
         }
     }

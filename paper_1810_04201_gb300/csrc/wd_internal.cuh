@@ -47,6 +47,22 @@ template <class R> __device__ __forceinline__ C<R> cmulc(C<R> a, C<R> b) {
 }
 template <class R> __device__ __forceinline__ C<R> cscale(R s, C<R> a) { return C<R>{s * a.re, s * a.im}; }
 
+// a * b + c as one fused multiply-add where the type has one
+template <class R> __device__ __forceinline__ R madd(R a, R b, R c) { return a * b + c; }
+template <> __device__ __forceinline__ double madd<double>(double a, double b, double c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ float madd<float>(float a, float b, float c) { return fmaf(a, b, c); }
+// s + a * b and s + conj(a) * b as chains of four multiply-adds
+template <class R> __device__ __forceinline__ C<R> cmac(C<R> s, C<R> a, C<R> b) {
+    const R re = madd(-a.im, b.im, madd(a.re, b.re, s.re));
+    const R im = madd(a.im, b.re, madd(a.re, b.im, s.im));
+    return C<R>{re, im};
+}
+template <class R> __device__ __forceinline__ C<R> cmacc(C<R> s, C<R> a, C<R> b) {
+    const R re = madd(a.im, b.im, madd(a.re, b.re, s.re));
+    const R im = madd(-a.im, b.re, madd(a.re, b.im, s.im));
+    return C<R>{re, im};
+}
+
 // ------------------------------------------------------------------ geometry
 struct Geom {
     int L[4];
