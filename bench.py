@@ -70,13 +70,21 @@ def load_peaks():
 FP64_PEAK_GFLOPS = 1250.0
 
 
-def csrc_hash() -> str:
+# the sources that define the plain Dslash kernel (the one the roofline object reports)
+DSLASH_SOURCES = ("df32.cuh", "wd_internal.cuh", "dslash.cuh", "dslash_apply.cu")
+
+
+def csrc_hash(read=None) -> str:
+    """Hash of the Dslash kernel sources; `read(name)` may supply another version of them."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1810_04201_gb300", "csrc")
-    for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh", ".h")):
+    for n in DSLASH_SOURCES:
+        if read is None:
             with open(os.path.join(d, n), "rb") as f:
-                h.update(n.encode() + f.read())
+                data = f.read()
+        else:
+            data = read(n)
+        h.update(n.encode() + data)
     return h.hexdigest()[:16]
 
 
@@ -252,6 +260,7 @@ def main():
                     help="time only the Dslash kernel on this lattice (profiling helper)")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--autotune", action="store_true", help="with --dslash-only: autotune the launch shape first")
     ap.add_argument("--compare", action="store_true",
                     help="c3: FP64 vs FP32 vs FP16-storage solves; c4: 12 sequential FP64 solves vs multi-RHS "
                          "and block CG; c5: batched persistent solve vs one-at-a-time FP64 solves")
@@ -291,6 +300,8 @@ def main():
     U, b = make_inputs(w, rank)
     lat = wd.Lattice(w["dims"])
     lat.set_gauge(U, recon=args.recon)
+    # the autotuner picks the thread-block shape of the Dslash for this lattice
+    tuned = {p: lat.autotune(wd.PRECS[p], nrhs) for p in sorted({"f64", inner})}
     fb = lat.pack(b)
     fx = lat.new_field(nrhs=nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -413,6 +424,7 @@ def main():
                    "true_rel_resid": max(r["true_rel_resid"] for r in results),
                    "operator_applications": n_apply},
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+            "autotuned_tiles": {p: {"site_tile": t[0], "rhs_tile": t[1]} for p, t in tuned.items()},
             "e2e": e2e}
     if args.sweep:
         line["dslash_sweep"] = sweep(wd, torch, flush, stream, args.recon)
@@ -573,6 +585,7 @@ def dslash_only(args):
     lat.set_gauge(gen.haar_links(dims, 3), recon=args.recon)
     b = gen.gaussian_source(dims, 4, nrhs=args.nrhs)
     pid = PREC_ID[args.prec]
+    tiles = lat.autotune(pid, args.nrhs) if args.autotune else None
     fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
     fo = lat.new_field(pid, args.nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -592,7 +605,7 @@ def dslash_only(args):
     ms = statistics.mean(ts)
     V = lat.V
     nb = V * (args.nrhs * 2 * SPINOR_BYTES[args.prec] + LINK_BYTES[(args.prec, args.recon)])
-    print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs,
+    print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs, "tiles": tiles,
                       "ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V * args.nrhs / ms / 1e6, 1),
                       "algorithmic_gbs": round(nb / ms / 1e6, 1), "bytes_per_launch": nb}))
 

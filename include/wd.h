@@ -153,7 +153,12 @@ wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, voi
  *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
  *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
  *              1: block CG (one Krylov space for all right-hand sides, FP64 only)
- *   rhs_tile   right-hand sides per thread block in the multi-RHS Dslash (0 = tuned) */
+ *   rhs_tile   right-hand sides per thread block in the multi-RHS Dslash (0 = tuned)
+ *   normal_eq  0: CGNR, D^dag D x = D^dag b (default).  1: CGNE, the form of the
+ *              paper's listing (section 2.2): D D^dag y = b from y = 0, then
+ *              x = D^dag y; the iterated residual is b - D x itself, tol applies
+ *              to ||b - D x|| / ||b||, and the initial guess in x is ignored.
+ *              Block CG and the batched solver use CGNR only. */
 typedef struct wd_cg_params {
     double tol;
     int max_iter;
@@ -162,6 +167,7 @@ typedef struct wd_cg_params {
     int nrhs;
     int block;
     int rhs_tile;
+    int normal_eq;
 } wd_cg_params;
 
 /* Per right-hand side result. */

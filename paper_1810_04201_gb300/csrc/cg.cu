@@ -20,7 +20,10 @@ namespace wd {
 
 // Record the FP64 (inner == F64) or mixed-precision solver.  hwhile / hif are the
 // conditional handles the loop kernels set (0 for the host-driven loop).
-template <int RECON, int SP>
+// NE = false: CGNR, A = D^dag D, rhs D^dag b.  NE = true: CGNE, the paper's form
+// (section 2.2): A = D D^dag, rhs b, iterate y (kept in the x field), x = D^dag y.
+// The two share every kernel; only which of D and D^dag comes first changes.
+template <int RECON, int SP, bool NE>
 static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                         cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif, Plan &plan) {
     GraphBuilder gb(&plan.setup);
@@ -47,16 +50,20 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
     vb.sc = f.sc;
     vb.state = f.state;
 
-    // ---- setup (FP64): db = D^dag b; t = D x0; r = db - D^dag t; p = r
+    // first (OP1) and second (OP2) operator of A: CGNR D then D^dag, CGNE D^dag then D
+    constexpr bool OP1 = NE, OP2 = !NE;
+    // ---- setup (FP64): db = rhs; t = OP1 x0; r = db - OP2 t; p = r
     {
         DslashArgs a = base;
         a.mask = 0;
         a.in = f.b; a.out = f.db;
+        if (NE) a.kappa = 0.0;  // D with kappa = 0 is the identity: db = b, |b|^2
         add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+        a.kappa = pl.kappa;
         a.in = f.x; a.out = f.t;
-        add_dslash<F64, RECON, false, EpXpay>(gb, a, pl.t64, false);
+        add_dslash<F64, RECON, OP1, EpXpay>(gb, a, pl.t64, false);
         a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
-        add_dslash<F64, RECON, true, EpSetupR>(gb, a, pl.t64, true);
+        add_dslash<F64, RECON, OP2, EpSetupR>(gb, a, pl.t64, true);
     }
     if (mixed) {
         VecArgs v = vb;
@@ -76,9 +83,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
             DslashArgs a = base;
             a.mask = 1;
             a.in = f.p; a.out = f.t;
-            add_dslash<F64, RECON, false, EpCG1>(bb, a, pl.t64, true);
+            add_dslash<F64, RECON, OP1, EpCG1>(bb, a, pl.t64, true);
             a.in = f.t; a.a0 = f.p; a.a1 = f.r; a.a2 = f.x;
-            add_dslash<F64, RECON, true, EpCG2>(bb, a, pl.t64, true);
+            add_dslash<F64, RECON, OP2, EpCG2>(bb, a, pl.t64, true);
             VecArgs v = vb;
             v.mask = 1;
             v.a = f.r; v.a_stride = s64; v.b = f.p; v.b_stride = s64; v.cond = hwhile;
@@ -91,9 +98,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
             a.in_stride = a.out_stride = a.a0_stride = a.a1_stride = sin;
             a.a2_stride = s32;
             a.in = f.ps; a.out = f.ts;
-            add_dslash<SP, RECON, false, EpCG1>(bb, a, pl.tin, true);
+            add_dslash<SP, RECON, OP1, EpCG1>(bb, a, pl.tin, true);
             a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
-            add_dslash<SP, RECON, true, EpCG2Mixed>(bb, a, pl.tin, true);
+            add_dslash<SP, RECON, OP2, EpCG2Mixed>(bb, a, pl.tin, true);
             plan.has_if = true;
             {
                 GraphBuilder ib(&plan.ifb);
@@ -104,9 +111,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
                 DslashArgs r = base;
                 r.mask = 2;
                 r.in = f.x; r.out = f.t;
-                add_dslash<F64, RECON, false, EpXpay>(ib, r, pl.t64, false);
+                add_dslash<F64, RECON, OP1, EpXpay>(ib, r, pl.t64, false);
                 r.in = f.t; r.a0 = f.db; r.a1 = f.r;
-                add_dslash<F64, RECON, true, EpReliable>(ib, r, pl.t64, true);
+                add_dslash<F64, RECON, OP2, EpReliable>(ib, r, pl.t64, true);
                 v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
                 add_vec(ib, k_convert<F64, SP>, v);
             }
@@ -118,20 +125,33 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
         }
     }
 
-    // ---- final FP64 check: t = D x, |b - t|^2; |db - D^dag t|^2
+    // ---- final FP64 check: t = D x, |b - t|^2; |D^dag b - D^dag t|^2
     gb.cur = &plan.fin;
     {
         DslashArgs a = base;
         a.mask = 0;
+        void *dbt = f.db;
+        if (NE) {
+            // x = D^dag y ; D^dag b (into p) and its norm for the normal-equation residual
+            a.in = f.x; a.out = f.t;
+            add_dslash<F64, RECON, true, EpXpay>(gb, a, pl.t64, false);
+            VecArgs v = vb;
+            v.mask = 0;
+            v.a = f.t; v.a_stride = s64; v.b = f.x; v.b_stride = s64;
+            add_vec(gb, k_convert<F64, F64>, v);
+            a.in = f.b; a.out = f.p;
+            add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+            dbt = f.p;
+        }
         a.in = f.x; a.out = f.t; a.a0 = f.b;
         add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
-        a.in = f.t; a.a0 = f.db;
+        a.in = f.t; a.a0 = dbt;
         add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
     }
 }
 
 // One CUDA graph: setup -> WHILE { pre -> IF { ifb } -> post } -> final.
-template <int RECON, int SP>
+template <int RECON, int SP, bool NE>
 static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                                cudaGraphExec_t *exec, std::vector<long long> &counts) {
     cudaGraph_t graph;
@@ -141,7 +161,7 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     e = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && SP != F64) e = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
     Plan plan;
-    if (e == cudaSuccess) record_plan<RECON, SP>(c, pl, f, g64, gin, hwhile, hif, plan);
+    if (e == cudaSuccess) record_plan<RECON, SP, NE>(c, pl, f, g64, gin, hwhile, hif, plan);
     std::vector<cudaGraphNode_t> deps;
     if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
     cudaGraph_t body = nullptr;
@@ -165,25 +185,39 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     return e;
 }
 
+template <int RECON, bool NE>
+static cudaError_t build_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                                cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    switch (pl.inner) {
+    case F64: return build_graph<RECON, F64, NE>(c, pl, f, g64, gin, exec, counts);
+    case F32: return build_graph<RECON, F32, NE>(c, pl, f, g64, gin, exec, counts);
+    case DF32: return build_graph<RECON, DF32, NE>(c, pl, f, g64, gin, exec, counts);
+    default: return build_graph<RECON, F16, NE>(c, pl, f, g64, gin, exec, counts);
+    }
+}
+
 template <int RECON>
 static cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                              cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    return pl.ne ? build_for_ne<RECON, true>(c, pl, f, g64, gin, exec, counts)
+                 : build_for_ne<RECON, false>(c, pl, f, g64, gin, exec, counts);
+}
+
+template <int RECON, bool NE>
+static void record_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                          Plan &plan) {
     switch (pl.inner) {
-    case F64: return build_graph<RECON, F64>(c, pl, f, g64, gin, exec, counts);
-    case F32: return build_graph<RECON, F32>(c, pl, f, g64, gin, exec, counts);
-    case DF32: return build_graph<RECON, DF32>(c, pl, f, g64, gin, exec, counts);
-    default: return build_graph<RECON, F16>(c, pl, f, g64, gin, exec, counts);
+    case F64: record_plan<RECON, F64, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F32: record_plan<RECON, F32, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case DF32: record_plan<RECON, DF32, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
+    default: record_plan<RECON, F16, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
     }
 }
 
 template <int RECON>
 static void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan) {
-    switch (pl.inner) {
-    case F64: record_plan<RECON, F64>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case F32: record_plan<RECON, F32>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case DF32: record_plan<RECON, DF32>(c, pl, f, g64, gin, 0, 0, plan); break;
-    default: record_plan<RECON, F16>(c, pl, f, g64, gin, 0, 0, plan); break;
-    }
+    if (pl.ne) record_for_ne<RECON, true>(c, pl, f, g64, gin, plan);
+    else record_for_ne<RECON, false>(c, pl, f, g64, gin, plan);
 }
 
 // The same plan launched kernel by kernel from the host; the active flags are read
@@ -231,8 +265,10 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (prm->inner_prec < 0 || prm->inner_prec >= kNumPrec) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad inner_prec");
     if (!(prm->tol > 0) || !std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad tol or kappa");
     if (b == x) return fail(c, WD_ERR_ARG, "wd_cg_solve: b and x must be distinct");
+    if (prm->normal_eq != 0 && prm->normal_eq != 1) return fail(c, WD_ERR_ARG, "wd_cg_solve: normal_eq must be 0 or 1");
     if (prm->block) {
         if (prm->inner_prec != WD_F64) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG runs in FP64 only");
+        if (prm->normal_eq) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG solves D^dag D only");
         return block_cg_solve(c, kappa, b, x, prm, res);
     }
     const Prec inner = (Prec)prm->inner_prec;
@@ -266,10 +302,11 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     f.counter = (unsigned *)tmp;
     f.state = (int *)((char *)tmp + 64);
 
-    SolverPlan pl{c->recon, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs)};
+    SolverPlan pl{c->recon, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs),
+                  prm->normal_eq ? 1 : 0};
     char key[256];
-    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
-             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile);
+    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d|%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
+             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne);
     const char *loop_env = getenv("WD_CG_LOOP");
     const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
     cudaGraphExec_t exec = nullptr;
@@ -307,7 +344,8 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
     WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
     WD_CUDA(c, cudaMemcpyAsync(f.b, b, s64, cudaMemcpyDeviceToDevice, c->stream));
-    WD_CUDA(c, cudaMemcpyAsync(f.x, x, s64, cudaMemcpyDeviceToDevice, c->stream));
+    if (pl.ne) WD_CUDA(c, cudaMemsetAsync(f.x, 0, s64, c->stream));  // CGNE starts from y = 0
+    else WD_CUDA(c, cudaMemcpyAsync(f.x, x, s64, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t e0, e1;
     WD_CUDA(c, cudaEventCreate(&e0));
     WD_CUDA(c, cudaEventCreate(&e1));

@@ -214,10 +214,10 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
 // handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
 // one site; Ep::finish runs once per thread after the loop (block and grid
 // reductions, solver scalars).
-// The same hopping sum as a rolled loop over the 8 hops (direction mu = hop / 2,
-// forward when hop is even).  The code of one hop is reused 8 times, so the
-// instruction footprint stays small; used for DF32, whose fully unrolled form is
-// large enough to miss in the instruction cache.
+// The same hopping sum as a loop over the 4 directions that is not unrolled.  The
+// code of one direction is reused 4 times, so the instruction footprint stays
+// small; used for DF32, whose fully unrolled form (about 9000 instructions per
+// site) is large enough to miss in the instruction cache.
 template <class R>
 __device__ __forceinline__ void project_rt(int mu, int sgn, const C<R> (&p)[12], C<R> (&h)[6]) {
     if (sgn > 0) {
@@ -256,37 +256,36 @@ __device__ __forceinline__ void accumulate_rt(int mu, int sgn, C<R> (&acc)[12], 
     }
 }
 
+// Each iteration holds the forward and the backward hop of one direction: two
+// independent chains for the scheduler.
 template <int P, int RECON, bool DAG, bool NC = true>
-__device__ __forceinline__ void hopping_rolled(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes,
-                                               int s, C<typename Real<P>::T> (&acc)[12]) {
+__device__ __forceinline__ void hopping_rolled_dir(const Geom &g, const void *in, const void *gauge,
+                                                   size_t gdir_bytes, int s, C<typename Real<P>::T> (&acc)[12]) {
     using R = typename Real<P>::T;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = C<R>{R(0), R(0)};
     const char *gb = reinterpret_cast<const char *>(gauge);
+    constexpr int SF = DAG ? +1 : -1;
 #pragma unroll 1
-    for (int hop = 0; hop < 8; ++hop) {
-        const int mu = hop >> 1;
-        const bool fwd = (hop & 1) == 0;
+    for (int mu = 0; mu < 4; ++mu) {
         const int L = g.L[mu], st = g.stride[mu];
         const int cm = (s / st) % L;
-        int sn;
-        bool flip;
-        if (fwd) {
-            sn = (cm == L - 1) ? s - (L - 1) * st : s + st;
-            flip = mu == 3 && g.antiperiodic && cm == L - 1;
-        } else {
-            sn = (cm == 0) ? s + (L - 1) * st : s - st;
-            flip = mu == 3 && g.antiperiodic && cm == 0;
-        }
-        // forward hop: projector 1 - gamma (D) or 1 + gamma (D^dag); backward: the opposite
-        const int sgn = fwd == DAG ? 1 : -1;
-        C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::template load<NC>(in, g.Vs, sn, p);
-        project_rt(mu, sgn, p, h);
-        LinkIO<P, RECON>::load(gb + (size_t)mu * gdir_bytes, g.Vs, fwd ? s : sn, u);
-        if (fwd) su3_mult<false>(u, h, w, flip);
-        else su3_mult<true>(u, h, w, flip);
-        accumulate_rt(mu, sgn, acc, w);
+        const int sf = (cm == L - 1) ? s - (L - 1) * st : s + st;
+        const int sb = (cm == 0) ? s + (L - 1) * st : s - st;
+        const bool ff = mu == 3 && g.antiperiodic && cm == L - 1;
+        const bool fb = mu == 3 && g.antiperiodic && cm == 0;
+        const char *gd = gb + (size_t)mu * gdir_bytes;
+        C<R> pf[12], pb[12], hf[6], hb[6], uf[9], ub[9], wf[6], wb[6];
+        SpinorIO<P>::template load<NC>(in, g.Vs, sf, pf);
+        SpinorIO<P>::template load<NC>(in, g.Vs, sb, pb);
+        LinkIO<P, RECON>::load(gd, g.Vs, s, uf);
+        LinkIO<P, RECON>::load(gd, g.Vs, sb, ub);
+        project_rt(mu, SF, pf, hf);
+        project_rt(mu, -SF, pb, hb);
+        su3_mult<false>(uf, hf, wf, ff);
+        su3_mult<true>(ub, hb, wb, fb);
+        accumulate_rt(mu, SF, acc, wf);
+        accumulate_rt(mu, -SF, acc, wb);
     }
 }
 
@@ -307,7 +306,7 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
         const int s = s0 + threadIdx.x;
         if (row && s < a.g.V) {
             C<R> acc[12];
-            if constexpr (P == DF32) hopping_rolled<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
             else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
             Ep::template site<P>(a, s, r, in, acc, st);
         }

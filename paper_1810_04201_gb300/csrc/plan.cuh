@@ -131,6 +131,7 @@ struct SolverPlan {
     int nrhs;
     Prec inner;
     DslashTiles t64, tin;
+    int ne;  // 0: CGNR on D^dag D x = D^dag b; 1: CGNE on D D^dag y = b, x = D^dag y
 };
 
 }  // namespace wd

@@ -27,7 +27,7 @@ MAX_RHS = 16
 class CGParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("block", ctypes.c_int),
-                ("rhs_tile", ctypes.c_int)]
+                ("rhs_tile", ctypes.c_int), ("normal_eq", ctypes.c_int)]
 
 
 class CGResult(ctypes.Structure):
@@ -199,13 +199,14 @@ class Lattice:
 
     # ------------------------------------------------------------------ solvers
     @staticmethod
-    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0):
-        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile)
+    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0, normal_eq=0):
+        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile, normal_eq)
 
     def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0,
-           raise_on_fail=True):
-        """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results."""
-        p = self.params(tol, max_iter, inner, delta, nrhs, block)
+           raise_on_fail=True, normal_eq=0):
+        """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results.
+        normal_eq=1 selects CGNE (D D^dag y = b, x = D^dag y)."""
+        p = self.params(tol, max_iter, inner, delta, nrhs, block, 0, normal_eq)
         res = (CGResult * nrhs)()
         st = self.lib.wd_cg_solve(self.ctx, float(kappa), ctypes.c_void_p(b.data_ptr()),
                                   ctypes.c_void_p(x.data_ptr()), ctypes.byref(p), res)
@@ -247,7 +248,7 @@ def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32
     ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
     bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
     xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
-    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0)
+    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0, 0)
     res = (CGResult * n)()
     st = lib.wd_cg_solve_batched(ctxs, ks, bp, xp, n, ctypes.byref(p), res)
     return [r.as_dict() for r in res], st

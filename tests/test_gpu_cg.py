@@ -197,3 +197,22 @@ def test_autotune_keeps_results(wd):
     lat.apply(kappa, f, o2, nrhs=4)
     # the per-site arithmetic does not depend on the launch shape
     np.testing.assert_array_equal(lat.unpack(o1, nrhs=4), lat.unpack(o2, nrhs=4))
+
+
+@pytest.mark.parametrize("inner", [0, 1, 3])
+def test_cgne_paper_form(wd, inner):
+    """CGNE (the paper's listing: D D^dag y = b, x = D^dag y) gives the oracle's solution."""
+    dims, kappa = (4, 4, 6, 4), 0.12
+    U = gen.haar_links(dims, seed=13)
+    b = gen.gaussian_source(dims, seed=14)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    _, ine = oracle.cgne(U, b, kappa, dims, tol=1e-10)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb, fx = lat.pack(b), lat.new_field()
+    res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner, normal_eq=1)
+    assert st == 0
+    assert res[0]["true_rel_resid_b"] <= 1e-10 * 1.01
+    assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+    if inner == 0:
+        assert abs(res[0]["iters"] - ine["iters"]) <= 1
