@@ -139,6 +139,14 @@ wd_status wd_normal_apply(wd_ctx *ctx, double kappa, const void *in, void *out, 
  * kernels overlap on the GPU (different streams or host threads) race on it. */
 wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
 
+/* The even-odd Schur operator (FP64): with D = [[1, -kappa H_eo], [-kappa H_oe, 1]] in
+ * even/odd blocks (D couples only opposite parities, section 2.1, Eq. (1)), writes
+ * (1 - kappa^2 H_eo H_oe) in_e (dagger = 0) or its adjoint (dagger = 1) into the even
+ * sites of out and zero into its odd sites.  in, out: WD_F64 fields (one right-hand
+ * side, full-lattice layout; the odd sites of in are ignored).  Needs even extents.
+ * Uses context-owned half-lattice temporaries. */
+wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, int dagger);
+
 /* Solver parameters.
  *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side)
  *   max_iter   iteration limit
@@ -158,7 +166,16 @@ wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, voi
  *              paper's listing (section 2.2): D D^dag y = b from y = 0, then
  *              x = D^dag y; the iterated residual is b - D x itself, tol applies
  *              to ||b - D x|| / ||b||, and the initial guess in x is ignored.
- *              Block CG and the batched solver use CGNR only. */
+ *              Block CG and the batched solver use CGNR only.
+ *   precondition WD_PRECOND_NONE, or WD_PRECOND_EO: even-odd (red-black) Schur
+ *              preconditioning.  D couples only sites of opposite parity, so on the
+ *              even sites D x = b reduces to (1 - kappa^2 H_eo H_oe) x_e = b_e +
+ *              kappa H_eo b_o, solved by CGNR on that operator, with x_o = b_o +
+ *              kappa H_oe x_e afterwards.  tol applies to the reduced system; the
+ *              residuals reported are those of D x = b on the whole lattice.  Needs
+ *              even extents; CGNR only (not with block or normal_eq). */
+#define WD_PRECOND_NONE 0
+#define WD_PRECOND_EO 1
 typedef struct wd_cg_params {
     double tol;
     int max_iter;
@@ -168,6 +185,7 @@ typedef struct wd_cg_params {
     int block;
     int rhs_tile;
     int normal_eq;
+    int precondition;
 } wd_cg_params;
 
 /* Per right-hand side result. */

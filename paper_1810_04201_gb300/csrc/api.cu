@@ -75,6 +75,47 @@ wd_status gauge_get(wd_ctx *c, Prec p, const void **out) {
     return WD_OK;
 }
 
+Geom eo_geom(const wd_ctx *c, int parity) {
+    Geom g = c->g;
+    g.V = c->g.V / 2;
+    g.Vs = (int)round_up((size_t)g.V, kSiteAlign);
+    g.eo_parity = parity;
+    return g;
+}
+
+template <int P, int RECON>
+static void gauge_pack_eo(const double *canon, void *dst, const Geom &g, int Vhs, size_t dir, cudaStream_t st) {
+    dim3 grid((g.V + 127) / 128, 4);
+    k_gauge_pack_eo<P, RECON><<<grid, 128, 0, st>>>(reinterpret_cast<const double2 *>(canon), dst, g, Vhs, dir);
+}
+
+wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes) {
+    if (!c->has_gauge) return fail(c, WD_ERR_STATE, "no gauge field set (call wd_set_gauge first)");
+    const int Vhs = eo_geom(c, 0).Vs;
+    const size_t dir = round_up(link_dir_bytes(p, c->recon, Vhs), 256);
+    if (!c->gauge_eo[p]) {
+        void *d = nullptr;
+        WD_CUDA(c, cudaMalloc(&d, 8 * dir));
+        if (c->recon == 12) {
+            if (p == F64) gauge_pack_eo<F64, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == F32) gauge_pack_eo<F32, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == DF32) gauge_pack_eo<DF32, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else gauge_pack_eo<F16, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+        } else {
+            if (p == F64) gauge_pack_eo<F64, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == F32) gauge_pack_eo<F32, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == DF32) gauge_pack_eo<DF32, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else gauge_pack_eo<F16, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+        }
+        WD_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+        c->gauge_eo[p] = d;
+    }
+    *out = c->gauge_eo[p];
+    *dir_bytes = dir;
+    return WD_OK;
+}
+
 DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs) {
     auto it = c->tiles.find(p * 64 + nrhs);
     if (it != c->tiles.end()) return it->second;
@@ -89,8 +130,10 @@ DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs) {
 wd_ctx::~wd_ctx() {
     for (auto &g : graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
     for (auto &w : ws) cudaFree(w.second);
-    for (int p = 0; p < kNumPrec; ++p)
+    for (int p = 0; p < kNumPrec; ++p) {
         if (gauge[p]) cudaFree(gauge[p]);
+        if (gauge_eo[p]) cudaFree(gauge_eo[p]);
+    }
     if (gauge_canon) cudaFree(gauge_canon);
 }
 
@@ -135,6 +178,7 @@ wd_status wd_create(wd_ctx **out, const int dims[4], int antiperiodic_t, void *s
     c->g.stride[2] = dims[0] * dims[1];
     c->g.stride[3] = dims[0] * dims[1] * dims[2];
     c->g.antiperiodic = antiperiodic_t ? 1 : 0;
+    c->g.eo_parity = -1;
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
@@ -163,11 +207,16 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     if (recon != 18 && recon != 12) return fail(c, WD_ERR_ARG, "wd_set_gauge: recon must be 18 or 12");
     const size_t bytes = (size_t)4 * c->g.V * 9 * 16;
     WD_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int p = 0; p < kNumPrec; ++p)
+    for (int p = 0; p < kNumPrec; ++p) {
         if (c->gauge[p]) {
             cudaFree(c->gauge[p]);
             c->gauge[p] = nullptr;
         }
+        if (c->gauge_eo[p]) {
+            cudaFree(c->gauge_eo[p]);
+            c->gauge_eo[p] = nullptr;
+        }
+    }
     if (!c->gauge_canon) WD_CUDA(c, cudaMalloc(&c->gauge_canon, bytes));
     WD_CUDA(c, cudaMemcpyAsync(c->gauge_canon, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                c->stream));

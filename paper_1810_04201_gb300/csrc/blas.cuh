@@ -129,46 +129,104 @@ template <int P> __global__ void k_zero(VecArgs v) {
     SpinorIO<P>::store(rp(v.b, v.b_stride, r), v.Vs, s, z);
 }
 
-// gauge: canonical (4 x V x 9 complex128, device) -> field of precision P, recon R
-template <int P, int RECON> __global__ void k_gauge_pack(const double2 *canon, void *dst, int V, int Vs,
-                                                         size_t dir_bytes) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x, mu = blockIdx.y;
-    if (s >= V) return;
-    const double2 *u = canon + ((size_t)mu * V + s) * 9;
-    char *base = reinterpret_cast<char *>(dst) + (size_t)mu * dir_bytes;
+// One link, canonical complex128 u[9] -> the layout of precision P and recon R,
+// at index idx of arrays with stride Vs starting at `base` (one direction).
+template <int P, int RECON>
+__device__ __forceinline__ void pack_link(const double2 *u, char *base, int Vs, int idx) {
     constexpr int n = RECON == 12 ? 6 : 9;
     if (P == F64) {
-        double2 *d = reinterpret_cast<double2 *>(base) + s;
+        double2 *d = reinterpret_cast<double2 *>(base) + idx;
         for (int e = 0; e < n; ++e) d[(size_t)e * Vs] = u[e];
     } else if (P == DF32) {
-        float4 *d = reinterpret_cast<float4 *>(base) + s;
+        float4 *d = reinterpret_cast<float4 *>(base) + idx;
         for (int e = 0; e < n; ++e) {
             const df re(u[e].x), im(u[e].y);
             d[(size_t)e * Vs] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
     } else if (P == F32) {
-        float4 *d = reinterpret_cast<float4 *>(base) + s;
+        float4 *d = reinterpret_cast<float4 *>(base) + idx;
         const int n4 = n / 2;
         for (int j = 0; j < n4; ++j)
             d[(size_t)j * Vs] = make_float4((float)u[2 * j].x, (float)u[2 * j].y, (float)u[2 * j + 1].x, (float)u[2 * j + 1].y);
         if (RECON == 18) {
-            float2 *e = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(base) + (size_t)4 * Vs) + s;
+            float2 *e = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(base) + (size_t)4 * Vs) + idx;
             *e = make_float2((float)u[8].x, (float)u[8].y);
         }
     } else {
-        uint4 *d = reinterpret_cast<uint4 *>(base) + s;
+        uint4 *d = reinterpret_cast<uint4 *>(base) + idx;
         auto h = [&](int e) { return f2h((float)u[e].x, (float)u[e].y); };
         if (RECON == 12) {
             *d = make_uint4(h(0), h(1), h(2), h(3));
-            uint2 *e = reinterpret_cast<uint2 *>(reinterpret_cast<uint4 *>(base) + Vs) + s;
+            uint2 *e = reinterpret_cast<uint2 *>(reinterpret_cast<uint4 *>(base) + Vs) + idx;
             *e = make_uint2(h(4), h(5));
         } else {
             d[0] = make_uint4(h(0), h(1), h(2), h(3));
             d[Vs] = make_uint4(h(4), h(5), h(6), h(7));
-            uint32_t *e = reinterpret_cast<uint32_t *>(reinterpret_cast<uint4 *>(base) + (size_t)2 * Vs) + s;
+            uint32_t *e = reinterpret_cast<uint32_t *>(reinterpret_cast<uint4 *>(base) + (size_t)2 * Vs) + idx;
             *e = h(8);
         }
     }
+}
+
+// gauge: canonical (4 x V x 9 complex128, device) -> field of precision P, recon R
+template <int P, int RECON> __global__ void k_gauge_pack(const double2 *canon, void *dst, int V, int Vs,
+                                                         size_t dir_bytes) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, mu = blockIdx.y;
+    if (s >= V) return;
+    pack_link<P, RECON>(canon + ((size_t)mu * V + s) * 9, reinterpret_cast<char *>(dst) + (size_t)mu * dir_bytes, Vs, s);
+}
+
+// gauge in checkerboard order: U_mu(n) -> parity of n, index n / 2 (arrays of stride Vhs)
+template <int P, int RECON> __global__ void k_gauge_pack_eo(const double2 *canon, void *dst, Geom g, int Vhs,
+                                                            size_t dir_bytes) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x, mu = blockIdx.y;
+    if (n >= g.V) return;
+    int rem = n;
+    const int x = rem % g.L[0]; rem /= g.L[0];
+    const int y = rem % g.L[1]; rem /= g.L[1];
+    const int z = rem % g.L[2];
+    const int t = rem / g.L[2];
+    const int par = (x + y + z + t) & 1;
+    char *base = reinterpret_cast<char *>(dst) + (size_t)(4 * par + mu) * dir_bytes;
+    pack_link<P, RECON>(canon + ((size_t)mu * g.V + n) * 9, base, Vhs, n >> 1);
+}
+
+__device__ __forceinline__ int site_parity(const Geom &g, int n) {
+    int rem = n;
+    const int x = rem % g.L[0]; rem /= g.L[0];
+    const int y = rem % g.L[1]; rem /= g.L[1];
+    const int z = rem % g.L[2];
+    const int t = rem / g.L[2];
+    return (x + y + z + t) & 1;
+}
+
+struct EoVecArgs {
+    VecArgs v;
+    int Vhs;  // site stride of the half fields
+    Geom g;   // full-lattice geometry
+};
+
+// FP64 full-lattice field (v.a, site stride v.Vs, RHS stride v.a_stride) -> even half
+// (v.b) and odd half (v.c) in checkerboard order (site stride Vhs, RHS stride v.b_stride)
+template <int DUMMY = 0> __global__ void k_split_eo(EoVecArgs e) {
+    const VecArgs &v = e.v;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (n >= v.V) return;
+    C<double> x[12];
+    SpinorIO<F64>::load(rp(v.a, v.a_stride, r), v.Vs, n, x);
+    void *dst = site_parity(e.g, n) ? const_cast<void *>(v.c) : v.b;
+    SpinorIO<F64>::store(rp(dst, v.b_stride, r), e.Vhs, n >> 1, x);
+}
+
+// the inverse: even (v.a) and odd (v.c) halves (RHS stride v.a_stride) -> full field (v.b)
+template <int DUMMY = 0> __global__ void k_join_eo(EoVecArgs e) {
+    const VecArgs &v = e.v;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (n >= v.V) return;
+    C<double> x[12];
+    const void *src = site_parity(e.g, n) ? v.c : v.a;
+    SpinorIO<F64>::load(rp(src, v.a_stride, r), e.Vhs, n >> 1, x);
+    SpinorIO<F64>::store(rp(v.b, v.b_stride, r), v.Vs, n, x);
 }
 
 }  // namespace wd

@@ -23,16 +23,19 @@ namespace wd {
 // NE = false: CGNR, A = D^dag D, rhs D^dag b.  NE = true: CGNE, the paper's form
 // (section 2.2): A = D D^dag, rhs b, iterate y (kept in the x field), x = D^dag y.
 // The two share every kernel; only which of D and D^dag comes first changes.
-template <int RECON, int SP, bool NE>
+// EO = true: even-odd preconditioning; the iteration runs on the even half with
+// the Schur operator, the odd half is rebuilt at the end (CGNR only).
+template <int RECON, int SP, bool NE, bool EO>
 static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                         cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif, Plan &plan) {
+    static_assert(!(NE && EO), "even-odd preconditioning is built for CGNR");
     GraphBuilder gb(&plan.setup);
-    const size_t s64 = spinor_bytes(F64, c->g.Vs), sin = spinor_bytes((Prec)SP, c->g.Vs),
-                 s32 = spinor_bytes(F32, c->g.Vs);
+    const Geom gw = EO ? f.eo.ge : c->g;  // geometry of the iterated fields
+    const size_t s64 = spinor_bytes(F64, gw.Vs), sin = spinor_bytes((Prec)SP, gw.Vs), s32 = spinor_bytes(F32, gw.Vs);
     const bool mixed = SP != F64;
 
     DslashArgs base{};
-    base.g = c->g;
+    base.g = gw;
     base.gauge = g64;
     base.gauge_dir = gauge_dir_bytes(c, F64);
     base.kappa = pl.kappa;
@@ -44,26 +47,46 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
     base.in_stride = base.out_stride = base.a0_stride = base.a1_stride = base.a2_stride = base.a3_stride = s64;
 
     VecArgs vb{};
-    vb.V = c->g.V;
-    vb.Vs = c->g.Vs;
+    vb.V = gw.V;
+    vb.Vs = gw.Vs;
     vb.nrhs = pl.nrhs;
     vb.sc = f.sc;
     vb.state = f.state;
 
     // first (OP1) and second (OP2) operator of A: CGNR D then D^dag, CGNE D^dag then D
     constexpr bool OP1 = NE, OP2 = !NE;
+    const size_t sfull = spinor_bytes(F64, c->g.Vs);
+    if constexpr (EO) {
+        // split b and x0 into halves; the Schur right-hand side b^ = b_e + kappa H_eo b_o
+        VecArgs v = vb;
+        v.V = c->g.V;
+        v.Vs = c->g.Vs;
+        v.mask = 0;
+        v.a = f.eo.bfull; v.a_stride = sfull; v.b = f.eo.be; v.c = f.eo.bo; v.b_stride = s64;
+        gb.kernel(k_split_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        v.a = f.eo.xfull; v.b = f.x; v.c = f.eo.xo;
+        gb.kernel(k_split_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        DslashArgs a = base;
+        a.mask = 0;
+        a.g = f.eo.ge;
+        a.gauge = f.eo.gauge[F64];
+        a.gauge_dir = f.eo.gdir[F64];
+        a.in = f.eo.bo; a.xsrc = f.eo.be; a.xsrc_stride = s64; a.out = f.b;
+        a.kappa = -pl.kappa;
+        add_dslash<F64, RECON, false, EpXpay, true>(gb, a, pl.t64, false);
+    }
     // ---- setup (FP64): db = rhs; t = OP1 x0; r = db - OP2 t; p = r
     {
         DslashArgs a = base;
         a.mask = 0;
         a.in = f.b; a.out = f.db;
         if (NE) a.kappa = 0.0;  // D with kappa = 0 is the identity: db = b, |b|^2
-        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+        add_op<F64, RECON, true, EpSetupDb, EO>(gb, a, pl.t64, true, f);
         a.kappa = pl.kappa;
         a.in = f.x; a.out = f.t;
-        add_dslash<F64, RECON, OP1, EpXpay>(gb, a, pl.t64, false);
+        add_op<F64, RECON, OP1, EpXpay, EO>(gb, a, pl.t64, false, f);
         a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
-        add_dslash<F64, RECON, OP2, EpSetupR>(gb, a, pl.t64, true);
+        add_op<F64, RECON, OP2, EpSetupR, EO>(gb, a, pl.t64, true, f);
     }
     if (mixed) {
         VecArgs v = vb;
@@ -83,9 +106,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
             DslashArgs a = base;
             a.mask = 1;
             a.in = f.p; a.out = f.t;
-            add_dslash<F64, RECON, OP1, EpCG1>(bb, a, pl.t64, true);
+            add_op<F64, RECON, OP1, EpCG1, EO>(bb, a, pl.t64, true, f);
             a.in = f.t; a.a0 = f.p; a.a1 = f.r; a.a2 = f.x;
-            add_dslash<F64, RECON, OP2, EpCG2>(bb, a, pl.t64, true);
+            add_op<F64, RECON, OP2, EpCG2, EO>(bb, a, pl.t64, true, f);
             VecArgs v = vb;
             v.mask = 1;
             v.a = f.r; v.a_stride = s64; v.b = f.p; v.b_stride = s64; v.cond = hwhile;
@@ -98,9 +121,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
             a.in_stride = a.out_stride = a.a0_stride = a.a1_stride = sin;
             a.a2_stride = s32;
             a.in = f.ps; a.out = f.ts;
-            add_dslash<SP, RECON, OP1, EpCG1>(bb, a, pl.tin, true);
+            add_op<SP, RECON, OP1, EpCG1, EO>(bb, a, pl.tin, true, f);
             a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
-            add_dslash<SP, RECON, OP2, EpCG2Mixed>(bb, a, pl.tin, true);
+            add_op<SP, RECON, OP2, EpCG2Mixed, EO>(bb, a, pl.tin, true, f);
             plan.has_if = true;
             {
                 GraphBuilder ib(&plan.ifb);
@@ -111,9 +134,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
                 DslashArgs r = base;
                 r.mask = 2;
                 r.in = f.x; r.out = f.t;
-                add_dslash<F64, RECON, OP1, EpXpay>(ib, r, pl.t64, false);
+                add_op<F64, RECON, OP1, EpXpay, EO>(ib, r, pl.t64, false, f);
                 r.in = f.t; r.a0 = f.db; r.a1 = f.r;
-                add_dslash<F64, RECON, OP2, EpReliable>(ib, r, pl.t64, true);
+                add_op<F64, RECON, OP2, EpReliable, EO>(ib, r, pl.t64, true, f);
                 v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
                 add_vec(ib, k_convert<F64, SP>, v);
             }
@@ -125,33 +148,55 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
         }
     }
 
-    // ---- final FP64 check: t = D x, |b - t|^2; |D^dag b - D^dag t|^2
+    // ---- final FP64 check: t = D x, |b - t|^2; |D^dag b - D^dag t|^2 (full lattice)
     gb.cur = &plan.fin;
-    {
-        DslashArgs a = base;
-        a.mask = 0;
-        void *dbt = f.db;
-        if (NE) {
-            // x = D^dag y ; D^dag b (into p) and its norm for the normal-equation residual
-            a.in = f.x; a.out = f.t;
-            add_dslash<F64, RECON, true, EpXpay>(gb, a, pl.t64, false);
-            VecArgs v = vb;
-            v.mask = 0;
-            v.a = f.t; v.a_stride = s64; v.b = f.x; v.b_stride = s64;
-            add_vec(gb, k_convert<F64, F64>, v);
-            a.in = f.b; a.out = f.p;
-            add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
-            dbt = f.p;
-        }
-        a.in = f.x; a.out = f.t; a.a0 = f.b;
-        add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
-        a.in = f.t; a.a0 = dbt;
-        add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
+    DslashArgs a = base;
+    a.mask = 0;
+    void *xf = f.x, *bf = f.b, *tf = f.t, *dbt = f.db;
+    if constexpr (EO) {
+        // x_o = b_o + kappa H_oe x_e, join the halves, then check on the full lattice
+        DslashArgs o = base;
+        o.mask = 0;
+        o.g = f.eo.go;
+        o.gauge = f.eo.gauge[F64];
+        o.gauge_dir = f.eo.gdir[F64];
+        o.in = f.x; o.xsrc = f.eo.bo; o.xsrc_stride = s64; o.out = f.eo.xo;
+        o.kappa = -pl.kappa;
+        add_dslash<F64, RECON, false, EpXpay, true>(gb, o, pl.t64, false);
+        VecArgs v = vb;
+        v.V = c->g.V;
+        v.Vs = c->g.Vs;
+        v.mask = 0;
+        v.a = f.x; v.c = f.eo.xo; v.a_stride = s64; v.b = f.eo.xfull; v.b_stride = sfull;
+        gb.kernel(k_join_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        a.g = c->g;
+        a.gauge = g64;
+        a.gauge_dir = gauge_dir_bytes(c, F64);
+        a.in_stride = a.out_stride = a.a0_stride = sfull;
+        xf = f.eo.xfull; bf = f.eo.bfull; tf = f.eo.tfull; dbt = f.eo.dbfull;
+        a.in = bf; a.out = dbt;
+        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
     }
+    if (NE) {
+        // x = D^dag y ; D^dag b (into p) and its norm for the normal-equation residual
+        a.in = f.x; a.out = f.t;
+        add_dslash<F64, RECON, true, EpXpay>(gb, a, pl.t64, false);
+        VecArgs v = vb;
+        v.mask = 0;
+        v.a = f.t; v.a_stride = s64; v.b = f.x; v.b_stride = s64;
+        add_vec(gb, k_convert<F64, F64>, v);
+        a.in = f.b; a.out = f.p;
+        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+        dbt = f.p;
+    }
+    a.in = xf; a.out = tf; a.a0 = bf;
+    add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
+    a.in = tf; a.a0 = dbt;
+    add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
 }
 
 // One CUDA graph: setup -> WHILE { pre -> IF { ifb } -> post } -> final.
-template <int RECON, int SP, bool NE>
+template <int RECON, int SP, bool NE, bool EO>
 static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                                cudaGraphExec_t *exec, std::vector<long long> &counts) {
     cudaGraph_t graph;
@@ -161,7 +206,7 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     e = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && SP != F64) e = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
     Plan plan;
-    if (e == cudaSuccess) record_plan<RECON, SP, NE>(c, pl, f, g64, gin, hwhile, hif, plan);
+    if (e == cudaSuccess) record_plan<RECON, SP, NE, EO>(c, pl, f, g64, gin, hwhile, hif, plan);
     std::vector<cudaGraphNode_t> deps;
     if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
     cudaGraph_t body = nullptr;
@@ -185,39 +230,41 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     return e;
 }
 
-template <int RECON, bool NE>
+template <int RECON, bool NE, bool EO>
 static cudaError_t build_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                                 cudaGraphExec_t *exec, std::vector<long long> &counts) {
     switch (pl.inner) {
-    case F64: return build_graph<RECON, F64, NE>(c, pl, f, g64, gin, exec, counts);
-    case F32: return build_graph<RECON, F32, NE>(c, pl, f, g64, gin, exec, counts);
-    case DF32: return build_graph<RECON, DF32, NE>(c, pl, f, g64, gin, exec, counts);
-    default: return build_graph<RECON, F16, NE>(c, pl, f, g64, gin, exec, counts);
+    case F64: return build_graph<RECON, F64, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case F32: return build_graph<RECON, F32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case DF32: return build_graph<RECON, DF32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    default: return build_graph<RECON, F16, NE, EO>(c, pl, f, g64, gin, exec, counts);
     }
 }
 
 template <int RECON>
 static cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                              cudaGraphExec_t *exec, std::vector<long long> &counts) {
-    return pl.ne ? build_for_ne<RECON, true>(c, pl, f, g64, gin, exec, counts)
-                 : build_for_ne<RECON, false>(c, pl, f, g64, gin, exec, counts);
+    if (pl.eo) return build_for_ne<RECON, false, true>(c, pl, f, g64, gin, exec, counts);
+    return pl.ne ? build_for_ne<RECON, true, false>(c, pl, f, g64, gin, exec, counts)
+                 : build_for_ne<RECON, false, false>(c, pl, f, g64, gin, exec, counts);
 }
 
-template <int RECON, bool NE>
+template <int RECON, bool NE, bool EO>
 static void record_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                           Plan &plan) {
     switch (pl.inner) {
-    case F64: record_plan<RECON, F64, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case F32: record_plan<RECON, F32, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case DF32: record_plan<RECON, DF32, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
-    default: record_plan<RECON, F16, NE>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F64: record_plan<RECON, F64, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F32: record_plan<RECON, F32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case DF32: record_plan<RECON, DF32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    default: record_plan<RECON, F16, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
     }
 }
 
 template <int RECON>
 static void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan) {
-    if (pl.ne) record_for_ne<RECON, true>(c, pl, f, g64, gin, plan);
-    else record_for_ne<RECON, false>(c, pl, f, g64, gin, plan);
+    if (pl.eo) record_for_ne<RECON, false, true>(c, pl, f, g64, gin, plan);
+    else if (pl.ne) record_for_ne<RECON, true, false>(c, pl, f, g64, gin, plan);
+    else record_for_ne<RECON, false, false>(c, pl, f, g64, gin, plan);
 }
 
 // The same plan launched kernel by kernel from the host; the active flags are read
@@ -266,6 +313,15 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (!(prm->tol > 0) || !std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad tol or kappa");
     if (b == x) return fail(c, WD_ERR_ARG, "wd_cg_solve: b and x must be distinct");
     if (prm->normal_eq != 0 && prm->normal_eq != 1) return fail(c, WD_ERR_ARG, "wd_cg_solve: normal_eq must be 0 or 1");
+    if (prm->precondition != WD_PRECOND_NONE && prm->precondition != WD_PRECOND_EO)
+        return fail(c, WD_ERR_ARG, "wd_cg_solve: unknown preconditioner");
+    const bool eo = prm->precondition == WD_PRECOND_EO;
+    if (eo) {
+        if (prm->block || prm->normal_eq)
+            return fail(c, WD_ERR_ARG, "wd_cg_solve: even-odd preconditioning is built for plain CGNR");
+        for (int mu = 0; mu < 4; ++mu)
+            if (c->g.L[mu] % 2) return fail(c, WD_ERR_ARG, "wd_cg_solve: even-odd preconditioning needs even extents");
+    }
     if (prm->block) {
         if (prm->inner_prec != WD_F64) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG runs in FP64 only");
         if (prm->normal_eq) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG solves D^dag D only");
@@ -278,19 +334,42 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     s = gauge_get(c, inner, &gin);
     if (s != WD_OK) return s;
 
-    const size_t s64 = spinor_bytes(F64, c->g.Vs) * nrhs;
+    // iterated fields live on the full lattice, or on the even half with even-odd
+    const Geom gw = eo ? eo_geom(c, 0) : c->g;
+    const std::string pre = eo ? "eo_" : "cg_";
+    const size_t sfull = spinor_bytes(F64, c->g.Vs) * nrhs;
+    const size_t s64 = spinor_bytes(F64, gw.Vs) * nrhs;
     Fields f{};
-    const char *n64[6] = {"cg_b", "cg_x", "cg_db", "cg_r", "cg_p", "cg_t"};
+    const char *n64[6] = {"b", "x", "db", "r", "p", "t"};
     void **p64[6] = {&f.b, &f.x, &f.db, &f.r, &f.p, &f.t};
     for (int i = 0; i < 6; ++i)
-        if ((s = ws_get(c, n64[i], s64, p64[i])) != WD_OK) return s;
+        if ((s = ws_get(c, pre + n64[i], s64, p64[i])) != WD_OK) return s;
     if (inner != F64) {
-        const size_t sin = spinor_bytes(inner, c->g.Vs) * nrhs;
+        const size_t sin = spinor_bytes(inner, gw.Vs) * nrhs;
         std::string sfx = inner == F32 ? "32" : inner == F16 ? "16" : "d32";
-        if ((s = ws_get(c, "cg_rs" + sfx, sin, &f.rs)) != WD_OK) return s;
-        if ((s = ws_get(c, "cg_ps" + sfx, sin, &f.ps)) != WD_OK) return s;
-        if ((s = ws_get(c, "cg_ts" + sfx, sin, &f.ts)) != WD_OK) return s;
-        if ((s = ws_get(c, "cg_xs", spinor_bytes(F32, c->g.Vs) * nrhs, &f.xs)) != WD_OK) return s;
+        if ((s = ws_get(c, pre + "rs" + sfx, sin, &f.rs)) != WD_OK) return s;
+        if ((s = ws_get(c, pre + "ps" + sfx, sin, &f.ps)) != WD_OK) return s;
+        if ((s = ws_get(c, pre + "ts" + sfx, sin, &f.ts)) != WD_OK) return s;
+        if ((s = ws_get(c, pre + "xs", spinor_bytes(F32, gw.Vs) * nrhs, &f.xs)) != WD_OK) return s;
+    }
+    if (eo) {
+        f.eo.ge = eo_geom(c, 0);
+        f.eo.go = eo_geom(c, 1);
+        if ((s = gauge_get_eo(c, F64, &f.eo.gauge[F64], &f.eo.gdir[F64])) != WD_OK) return s;
+        if ((s = gauge_get_eo(c, inner, &f.eo.gauge[inner], &f.eo.gdir[inner])) != WD_OK) return s;
+        if ((s = ws_get(c, "eo_tmp64", s64, &f.eo.tmp64)) != WD_OK) return s;
+        if (inner != F64 &&
+            (s = ws_get(c, std::string("eo_tmps") + std::to_string((int)inner), spinor_bytes(inner, gw.Vs) * nrhs,
+                        &f.eo.tmps)) != WD_OK)
+            return s;
+        const char *nh[3] = {"eo_be", "eo_bo", "eo_xo"};
+        void **ph[3] = {&f.eo.be, &f.eo.bo, &f.eo.xo};
+        for (int i = 0; i < 3; ++i)
+            if ((s = ws_get(c, nh[i], s64, ph[i])) != WD_OK) return s;
+        const char *nf[4] = {"eo_bfull", "eo_xfull", "eo_tfull", "eo_dbfull"};
+        void **pf[4] = {&f.eo.bfull, &f.eo.xfull, &f.eo.tfull, &f.eo.dbfull};
+        for (int i = 0; i < 4; ++i)
+            if ((s = ws_get(c, nf[i], sfull, pf[i])) != WD_OK) return s;
     }
     void *tmp;
     if ((s = ws_get(c, "cg_scalars", sizeof(Scalars) * WD_MAX_RHS, &tmp)) != WD_OK) return s;
@@ -303,10 +382,10 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     f.state = (int *)((char *)tmp + 64);
 
     SolverPlan pl{c->recon, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs),
-                  prm->normal_eq ? 1 : 0};
+                  prm->normal_eq ? 1 : 0, eo ? 1 : 0};
     char key[256];
-    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d|%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
-             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne);
+    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
+             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo);
     const char *loop_env = getenv("WD_CG_LOOP");
     const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
     cudaGraphExec_t exec = nullptr;
@@ -343,9 +422,10 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     }
     WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
     WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
-    WD_CUDA(c, cudaMemcpyAsync(f.b, b, s64, cudaMemcpyDeviceToDevice, c->stream));
-    if (pl.ne) WD_CUDA(c, cudaMemsetAsync(f.x, 0, s64, c->stream));  // CGNE starts from y = 0
-    else WD_CUDA(c, cudaMemcpyAsync(f.x, x, s64, cudaMemcpyDeviceToDevice, c->stream));
+    void *bin = eo ? f.eo.bfull : f.b, *xin = eo ? f.eo.xfull : f.x;
+    WD_CUDA(c, cudaMemcpyAsync(bin, b, sfull, cudaMemcpyDeviceToDevice, c->stream));
+    if (pl.ne) WD_CUDA(c, cudaMemsetAsync(xin, 0, sfull, c->stream));  // CGNE starts from y = 0
+    else WD_CUDA(c, cudaMemcpyAsync(xin, x, sfull, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t e0, e1;
     WD_CUDA(c, cudaEventCreate(&e0));
     WD_CUDA(c, cudaEventCreate(&e1));
@@ -354,7 +434,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (host_loop) WD_CUDA(c, run_host_loop(c, hplan, f, nrhs, prm->max_iter, &host_launched));
     else WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
     WD_CUDA(c, cudaEventRecord(e1, c->stream));
-    WD_CUDA(c, cudaMemcpyAsync(x, f.x, s64, cudaMemcpyDeviceToDevice, c->stream));
+    WD_CUDA(c, cudaMemcpyAsync(x, xin, sfull, cudaMemcpyDeviceToDevice, c->stream));
     WD_CUDA(c, cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream));
     int st[2];
     WD_CUDA(c, cudaMemcpyAsync(st, f.state, sizeof st, cudaMemcpyDeviceToHost, c->stream));

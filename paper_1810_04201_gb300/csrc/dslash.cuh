@@ -40,6 +40,8 @@ struct DslashArgs {
     unsigned long long cond;   // cudaGraphConditionalHandle to set (0 = none)
     int *state;                // solver-wide counters
     const int *run_flag;       // when set and zero, the whole launch returns at once
+    const void *xsrc;          // field added by the xpay epilogues (nullptr: the hopping input)
+    size_t xsrc_stride;
 };
 
 template <class R> __device__ __forceinline__ const void *rhs_ptr(const void *b, size_t stride, int r) {
@@ -289,26 +291,129 @@ __device__ __forceinline__ void hopping_rolled_dir(const Geom &g, const void *in
     }
 }
 
+// ---------------------------------------------------------------- checkerboard
+// Even-odd fields hold one parity of the lattice: the site with full index n
+// (parity (x+y+z+t) mod 2) sits at n / 2 of its parity's arrays (all extents
+// even).  Links are stored the same way, per parity: U_mu(n) at n / 2 of the
+// parity of n, so the forward hop reads the output site's own parity and the
+// backward hop reads U_mu(n - mu) at the neighbour's index.  gauge points to
+// parity 0; parity 1 follows 4 * gdir_bytes later.
+__device__ __forceinline__ int eo_full_index(const Geom &g, int k, int &x, int &y, int &z, int &t) {
+    const int lxh = g.L[0] >> 1;
+    int r = k / lxh;
+    const int xh = k - r * lxh;
+    y = r % g.L[1];
+    r /= g.L[1];
+    z = r % g.L[2];
+    t = r / g.L[2];
+    x = 2 * xh + ((g.eo_parity + y + z + t) & 1);
+    return x + g.stride[1] * y + g.stride[2] * z + g.stride[3] * t;
+}
+
+template <int P, int RECON, bool DAG, int MU, bool NC = true>
+__device__ __forceinline__ void hop_dir_eo(const Geom &g, const void *in, const char *gp, const char *gq, int k, int n,
+                                           int c, C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+    constexpr int SF = DAG ? +1 : -1;
+    const int L = g.L[MU], st = g.stride[MU];
+    {
+        const int nf = (c == L - 1) ? n - (L - 1) * st : n + st;
+        C<R> p[12], h[6], w[6], u[9];
+        SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, p);
+        project<MU, SF>(p, h);
+        LinkIO<P, RECON>::load(gp, g.Vs, k, u);
+        su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
+        accumulate<MU, SF>(acc, w);
+    }
+    {
+        const int nb = (c == 0) ? n + (L - 1) * st : n - st;
+        C<R> p[12], h[6], w[6], u[9];
+        SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, p);
+        project<MU, -SF>(p, h);
+        LinkIO<P, RECON>::load(gq, g.Vs, nb >> 1, u);
+        su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+        accumulate<MU, -SF>(acc, w);
+    }
+}
+
+template <int P, int RECON, bool DAG, bool NC = true>
+__device__ __forceinline__ void hopping_eo(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes, int k,
+                                           C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = C<R>{R(0), R(0)};
+    int x, y, z, t;
+    const int n = eo_full_index(g, k, x, y, z, t);
+    const char *gp = reinterpret_cast<const char *>(gauge) + (size_t)(4 * g.eo_parity) * gdir_bytes;
+    const char *gq = reinterpret_cast<const char *>(gauge) + (size_t)(4 * (1 - g.eo_parity)) * gdir_bytes;
+    hop_dir_eo<P, RECON, DAG, 0, NC>(g, in, gp, gq, k, n, x, acc);
+    hop_dir_eo<P, RECON, DAG, 1, NC>(g, in, gp + gdir_bytes, gq + gdir_bytes, k, n, y, acc);
+    hop_dir_eo<P, RECON, DAG, 2, NC>(g, in, gp + 2 * gdir_bytes, gq + 2 * gdir_bytes, k, n, z, acc);
+    hop_dir_eo<P, RECON, DAG, 3, NC>(g, in, gp + 3 * gdir_bytes, gq + 3 * gdir_bytes, k, n, t, acc);
+}
+
+// checkerboard form of the rolled DF32 loop
+template <int P, int RECON, bool DAG, bool NC = true>
+__device__ __forceinline__ void hopping_rolled_dir_eo(const Geom &g, const void *in, const void *gauge,
+                                                      size_t gdir_bytes, int k, C<typename Real<P>::T> (&acc)[12]) {
+    using R = typename Real<P>::T;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = C<R>{R(0), R(0)};
+    int x, y, z, t;
+    const int n = eo_full_index(g, k, x, y, z, t);
+    const char *gp = reinterpret_cast<const char *>(gauge) + (size_t)(4 * g.eo_parity) * gdir_bytes;
+    const char *gq = reinterpret_cast<const char *>(gauge) + (size_t)(4 * (1 - g.eo_parity)) * gdir_bytes;
+    constexpr int SF = DAG ? +1 : -1;
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        const int L = g.L[mu], st = g.stride[mu];
+        const int cm = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+        const int nf = (cm == L - 1) ? n - (L - 1) * st : n + st;
+        const int nb = (cm == 0) ? n + (L - 1) * st : n - st;
+        const bool ff = mu == 3 && g.antiperiodic && cm == L - 1;
+        const bool fb = mu == 3 && g.antiperiodic && cm == 0;
+        C<R> pf[12], pb[12], hf[6], hb[6], uf[9], ub[9], wf[6], wb[6];
+        SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, pf);
+        SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, pb);
+        LinkIO<P, RECON>::load(gp + (size_t)mu * gdir_bytes, g.Vs, k, uf);
+        LinkIO<P, RECON>::load(gq + (size_t)mu * gdir_bytes, g.Vs, nb >> 1, ub);
+        project_rt(mu, SF, pf, hf);
+        project_rt(mu, -SF, pb, hb);
+        su3_mult<false>(uf, hf, wf, ff);
+        su3_mult<true>(ub, hb, wb, fb);
+        accumulate_rt(mu, SF, acc, wf);
+        accumulate_rt(mu, -SF, acc, wb);
+    }
+}
+
 // Register budget: the FP32 and FP16 kernels are memory-bound and want many
 // resident warps, so they are held to 3 blocks of 256 threads per SM (at most 85
 // registers); FP64 and DF32 are arithmetic-bound and keep the compiler's choice.
 template <int P> constexpr int dslash_min_blocks() { return (P == F32 || P == F16) ? 3 : 0; }
 
-template <int P, int RECON, bool DAG, class Ep>
+template <int P, int RECON, bool DAG, class Ep, bool EO = false>
 __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(DslashArgs a) {
     using R = typename Real<P>::T;
     if (a.run_flag && *a.run_flag == 0) return;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     const bool row = r < a.nrhs && row_on(a.sc, a.mask, r);
-    const void *in = rhs_ptr<R>(a.in, a.in_stride, r < a.nrhs ? r : 0);
+    const int rr = r < a.nrhs ? r : 0;
+    const void *in = rhs_ptr<R>(a.in, a.in_stride, rr);
+    // the field the xpay epilogues add: the hopping input unless another is given
+    const void *xin = a.xsrc ? rhs_ptr<R>(a.xsrc, a.xsrc_stride, rr) : in;
     typename Ep::State st{};
     for (int s0 = blockIdx.x * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
         const int s = s0 + threadIdx.x;
         if (row && s < a.g.V) {
             C<R> acc[12];
-            if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-            else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-            Ep::template site<P>(a, s, r, in, acc, st);
+            if constexpr (EO) {
+                if constexpr (P == DF32) hopping_rolled_dir_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                else hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            } else {
+                if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+            }
+            Ep::template site<P>(a, s, r, xin, acc, st);
         }
     }
     Ep::template finish<P>(a, r, row, st);
@@ -327,6 +432,21 @@ struct EpXpay {
 #pragma unroll
         for (int c = 0; c < 12; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
         SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &, int, bool, State &) {}
+};
+
+// out = -kappa * hop (no added field); kappa = -1 gives the bare hopping term
+struct EpHop {
+    struct State {};
+    template <int P, class R>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *, C<R> (&acc)[12],
+                                                State &) {
+        const R k = R(-a.kappa);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = C<R>{k * acc[c].re, k * acc[c].im};
+        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, acc);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &, int, bool, State &) {}

@@ -102,6 +102,17 @@ static dim3 reduce_grid(K kernel, const Geom &g, DslashTiles t, int nrhs) {
     return dim3(need < cap ? need : cap, (nrhs + t.rhs_tile - 1) / t.rhs_tile);
 }
 
+// Even-odd preconditioning: the solver works on the even half of the lattice
+// with the Schur operator 1 - kappa^2 H_eo H_oe; these are its extra operands.
+struct EoInfo {
+    Geom ge, go;                          // checkerboard geometry, output parity 0 / 1
+    const void *gauge[kNumPrec];          // checkerboard gauge per precision
+    size_t gdir[kNumPrec];
+    void *tmp64, *tmps;                   // odd-parity temporaries (FP64, inner precision)
+    void *bfull, *xfull, *tfull, *dbfull; // full-lattice fields for the split, join and final check
+    void *be, *bo, *xo;                   // even / odd halves
+};
+
 struct Fields {
     void *b, *x, *db, *r, *p, *t;      // FP64
     void *rs, *ps, *ts, *xs;            // inner precision (xs FP32)
@@ -109,11 +120,12 @@ struct Fields {
     double *partial;
     unsigned *counter;
     int *state;
+    EoInfo eo;
 };
 
-template <int P, int RECON, bool DAG, class Ep>
+template <int P, int RECON, bool DAG, class Ep, bool EO = false>
 static void add_dslash(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool reduce) {
-    auto k = dslash_kernel<P, RECON, DAG, Ep>;
+    auto k = dslash_kernel<P, RECON, DAG, Ep, EO>;
     dim3 block(t.site_tile, t.rhs_tile);
     dim3 grid = reduce ? reduce_grid(k, a.g, t, a.nrhs)
                        : dim3((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
@@ -132,6 +144,40 @@ struct SolverPlan {
     Prec inner;
     DslashTiles t64, tin;
     int ne;  // 0: CGNR on D^dag D x = D^dag b; 1: CGNE on D D^dag y = b, x = D^dag y
+    int eo;  // 1: even-odd preconditioned (Schur complement on the even sites)
 };
+
+// One application of the solver's operator: D (or D^dag) on the full lattice, or,
+// with even-odd preconditioning, the Schur operator 1 - kappa^2 H_eo H_oe (or its
+// adjoint) as two checkerboard kernels: a bare hop into an odd temporary, then
+// the hop back with the epilogue, which adds the even input.
+template <int P, int RECON, bool DAG, class Ep, bool EO>
+static void add_op(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool reduce, const Fields &f) {
+    if constexpr (!EO) {
+        add_dslash<P, RECON, DAG, Ep>(gb, a, t, reduce);
+    } else {
+        const size_t sp = spinor_bytes((Prec)P, f.eo.ge.Vs);
+        void *tmp = P == F64 ? f.eo.tmp64 : f.eo.tmps;
+        DslashArgs h = a;
+        h.g = f.eo.go;
+        h.gauge = f.eo.gauge[P];
+        h.gauge_dir = f.eo.gdir[P];
+        h.out = tmp;
+        h.out_stride = sp;
+        h.kappa = -1.0;
+        h.xsrc = nullptr;
+        add_dslash<P, RECON, DAG, EpHop, true>(gb, h, t, false);
+        DslashArgs e = a;
+        e.g = f.eo.ge;
+        e.gauge = f.eo.gauge[P];
+        e.gauge_dir = f.eo.gdir[P];
+        e.xsrc = a.in;
+        e.xsrc_stride = a.in_stride;
+        e.in = tmp;
+        e.in_stride = sp;
+        e.kappa = a.kappa * a.kappa;
+        add_dslash<P, RECON, DAG, Ep, true>(gb, e, t, reduce);
+    }
+}
 
 }  // namespace wd

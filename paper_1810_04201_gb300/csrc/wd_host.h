@@ -23,6 +23,11 @@ wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);
 // device gauge field of precision p at the context's recon (created on first use)
 wd_status gauge_get(wd_ctx *c, Prec p, const void **out);
 size_t gauge_dir_bytes(const wd_ctx *c, Prec p);
+// checkerboard gauge copy (parity-major, see dslash.cuh) of precision p, and its
+// direction stride in bytes
+wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes);
+// geometry of one parity of the lattice (all extents even)
+Geom eo_geom(const wd_ctx *c, int parity);
 
 DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs);
 

@@ -66,10 +66,11 @@ template <class R> __device__ __forceinline__ C<R> cmacc(C<R> s, C<R> a, C<R> b)
 // ------------------------------------------------------------------ geometry
 struct Geom {
     int L[4];
-    int V;
+    int V;           // output sites of a launch (V, or V/2 on one parity)
     int Vs;          // site stride of field arrays (V rounded up to kSiteAlign)
-    int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz (full-lattice strides)
     int antiperiodic;
+    int eo_parity;   // -1: full lattice; 0 / 1: checkerboard fields, output on this parity
 };
 
 // ------------------------------------------------------------------ field sizes
@@ -426,6 +427,7 @@ struct wd_ctx {
     int recon = 18;
     bool has_gauge = false;
     void *gauge[wd::kNumPrec] = {};                    // per precision (at this->recon)
+    void *gauge_eo[wd::kNumPrec] = {};                 // checkerboard copies, per precision
     double *gauge_canon = nullptr;                     // FP64 canonical copy on device
     std::string last_error;
     long long launches = 0;

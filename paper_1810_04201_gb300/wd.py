@@ -27,7 +27,7 @@ MAX_RHS = 16
 class CGParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("block", ctypes.c_int),
-                ("rhs_tile", ctypes.c_int), ("normal_eq", ctypes.c_int)]
+                ("rhs_tile", ctypes.c_int), ("normal_eq", ctypes.c_int), ("precondition", ctypes.c_int)]
 
 
 class CGResult(ctypes.Structure):
@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "wd_apply_dagger": ([P, D, P, P, I, I], I),
         "wd_normal_apply": ([P, D, P, P, I, I], I),
         "wd_normal_apply_noalloc": ([P, D, P, P, I, I], I),
+        "wd_apply_schur": ([P, D, P, P, I], I),
         "wd_cg_solve": ([P, D, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
         "wd_cg_solve_canonical": ([P, D, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult)], I),
         "wd_cg_solve_batched": ([PP, ctypes.POINTER(D), PP, PP, I, ctypes.POINTER(CGParams),
@@ -190,6 +191,12 @@ class Lattice:
                                              ctypes.c_void_p(dst.data_ptr()), prec, nrhs), "wd_normal_apply")
         return dst
 
+    def apply_schur(self, kappa, src, dst, dagger=False):
+        """Even sites of dst = (1 - kappa^2 H_eo H_oe) src_e (or its adjoint), odd sites = 0 (FP64)."""
+        self._check(self.lib.wd_apply_schur(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
+                                            ctypes.c_void_p(dst.data_ptr()), int(bool(dagger))), "wd_apply_schur")
+        return dst
+
     def normal_apply_noalloc(self, kappa, src, dst, prec=WD_F64, nrhs=1):
         """D^dag D through the entry point that allocates no device memory (fixed 16 MiB scratch)."""
         self._check(self.lib.wd_normal_apply_noalloc(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
@@ -199,14 +206,15 @@ class Lattice:
 
     # ------------------------------------------------------------------ solvers
     @staticmethod
-    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0, normal_eq=0):
-        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile, normal_eq)
+    def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0, normal_eq=0,
+               precondition=0):
+        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile, normal_eq, precondition)
 
     def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0,
-           raise_on_fail=True, normal_eq=0):
+           raise_on_fail=True, normal_eq=0, precondition=0):
         """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results.
-        normal_eq=1 selects CGNE (D D^dag y = b, x = D^dag y)."""
-        p = self.params(tol, max_iter, inner, delta, nrhs, block, 0, normal_eq)
+        normal_eq=1 selects CGNE (D D^dag y = b, x = D^dag y); precondition=1 even-odd."""
+        p = self.params(tol, max_iter, inner, delta, nrhs, block, 0, normal_eq, precondition)
         res = (CGResult * nrhs)()
         st = self.lib.wd_cg_solve(self.ctx, float(kappa), ctypes.c_void_p(b.data_ptr()),
                                   ctypes.c_void_p(x.data_ptr()), ctypes.byref(p), res)
@@ -215,10 +223,10 @@ class Lattice:
         return [r.as_dict() for r in res], st
 
     def cg_canonical(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1,
-                     raise_on_fail=True):
+                     raise_on_fail=True, precondition=0):
         """End-to-end solve on canonical host arrays (numpy complex128, pinned torch CPU tensors
         allowed) or device tensors; x is overwritten with the solution."""
-        p = self.params(tol, max_iter, inner, delta, nrhs, 0)
+        p = self.params(tol, max_iter, inner, delta, nrhs, 0, 0, 0, precondition)
         res = (CGResult * nrhs)()
         if isinstance(b, torch.Tensor):
             on_dev = int(b.is_cuda)
@@ -248,7 +256,7 @@ def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32
     ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
     bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
     xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
-    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0, 0)
+    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0, 0, 0)
     res = (CGResult * n)()
     st = lib.wd_cg_solve_batched(ctxs, ks, bp, xp, n, ctypes.byref(p), res)
     return [r.as_dict() for r in res], st
