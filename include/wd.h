@@ -171,9 +171,11 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *              preconditioning.  D couples only sites of opposite parity, so on the
  *              even sites D x = b reduces to (1 - kappa^2 H_eo H_oe) x_e = b_e +
  *              kappa H_eo b_o, solved by CGNR on that operator, with x_o = b_o +
- *              kappa H_oe x_e afterwards.  tol applies to the reduced system; the
- *              residuals reported are those of D x = b on the whole lattice.  Needs
- *              even extents; CGNR only (not with block or normal_eq). */
+ *              kappa H_oe x_e afterwards.  The reduced system is solved to tol / 2
+ *              and resumed from its solution with a tighter tolerance (at most three
+ *              times) until the recomputed FP64 residual of D x = b on the whole
+ *              lattice meets tol; iterations are summed.  Needs even extents; CGNR
+ *              only (not with block or normal_eq). */
 #define WD_PRECOND_NONE 0
 #define WD_PRECOND_EO 1
 typedef struct wd_cg_params {

@@ -409,54 +409,79 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         }
     }
 
-    // per-RHS state
+    // per-RHS state.  With even-odd preconditioning tol applies to the reduced system,
+    // so the solve runs with half of it and is resumed from its own solution, with a
+    // tighter reduced tolerance, until the recomputed full-lattice residual meets tol.
     std::vector<Scalars> h(nrhs);
     const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec);
-    for (int r = 0; r < nrhs; ++r) {
-        std::memset(&h[r], 0, sizeof(Scalars));
-        h[r].tol2 = prm->tol * prm->tol;
-        h[r].max_iter = prm->max_iter;
-        h[r].delta2 = delta * delta;
-        h[r].active = 1;
-        h[r].status = WD_ERR_NOT_CONVERGED;
-    }
-    WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
-    WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
     void *bin = eo ? f.eo.bfull : f.b, *xin = eo ? f.eo.xfull : f.x;
     WD_CUDA(c, cudaMemcpyAsync(bin, b, sfull, cudaMemcpyDeviceToDevice, c->stream));
     if (pl.ne) WD_CUDA(c, cudaMemsetAsync(xin, 0, sfull, c->stream));  // CGNE starts from y = 0
     else WD_CUDA(c, cudaMemcpyAsync(xin, x, sfull, cudaMemcpyDeviceToDevice, c->stream));
-    cudaEvent_t e0, e1;
-    WD_CUDA(c, cudaEventCreate(&e0));
-    WD_CUDA(c, cudaEventCreate(&e1));
-    WD_CUDA(c, cudaEventRecord(e0, c->stream));
-    long long host_launched = 0;
-    if (host_loop) WD_CUDA(c, run_host_loop(c, hplan, f, nrhs, prm->max_iter, &host_launched));
-    else WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
-    WD_CUDA(c, cudaEventRecord(e1, c->stream));
-    WD_CUDA(c, cudaMemcpyAsync(x, xin, sfull, cudaMemcpyDeviceToDevice, c->stream));
-    WD_CUDA(c, cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream));
-    int st[2];
-    WD_CUDA(c, cudaMemcpyAsync(st, f.state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
-    WD_CUDA(c, cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (host_loop) {
-        c->launches = host_launched;
-    } else {
-        const std::vector<long long> &cnt = c->graph_info[key];
-        c->launches = cnt[0] + (long long)st[0] * cnt[1] + (long long)st[1] * cnt[2] + cnt[3];
+    double tol_run = eo ? 0.5 * prm->tol : prm->tol;
+    std::vector<int> iters(nrhs, 0), reliable(nrhs, 0);
+    float ms_total = 0.f;
+    long long launches = 0;
+    const int attempts = eo ? 4 : 1;
+    for (int attempt = 0; attempt < attempts; ++attempt) {
+        for (int r = 0; r < nrhs; ++r) {
+            std::memset(&h[r], 0, sizeof(Scalars));
+            h[r].tol2 = tol_run * tol_run;
+            h[r].max_iter = prm->max_iter - iters[r] > 0 ? prm->max_iter - iters[r] : 0;
+            h[r].delta2 = delta * delta;
+            h[r].active = 1;
+            h[r].status = WD_ERR_NOT_CONVERGED;
+        }
+        WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
+        WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
+        cudaEvent_t e0, e1;
+        WD_CUDA(c, cudaEventCreate(&e0));
+        WD_CUDA(c, cudaEventCreate(&e1));
+        WD_CUDA(c, cudaEventRecord(e0, c->stream));
+        long long host_launched = 0;
+        if (host_loop) WD_CUDA(c, run_host_loop(c, hplan, f, nrhs, h[0].max_iter, &host_launched));
+        else WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
+        WD_CUDA(c, cudaEventRecord(e1, c->stream));
+        WD_CUDA(c, cudaMemcpyAsync(h.data(), f.sc, sizeof(Scalars) * nrhs, cudaMemcpyDeviceToHost, c->stream));
+        int st[2];
+        WD_CUDA(c, cudaMemcpyAsync(st, f.state, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+        WD_CUDA(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ms_total += ms;
+        if (host_loop) {
+            launches += host_launched;
+        } else {
+            const std::vector<long long> &cnt = c->graph_info[key];
+            launches += cnt[0] + (long long)st[0] * cnt[1] + (long long)st[1] * cnt[2] + cnt[3];
+        }
+        double worst_resid = 0.0;
+        bool all_ok = true;
+        for (int r = 0; r < nrhs; ++r) {
+            iters[r] += h[r].iter;
+            reliable[r] += h[r].reliable;
+            all_ok &= h[r].status == WD_OK;
+            const double tr = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
+            worst_resid = tr > worst_resid ? tr : worst_resid;
+        }
+        if (!eo || !all_ok || worst_resid <= prm->tol || !(worst_resid > 0)) break;
+        tol_run *= 0.5 * prm->tol / worst_resid;
+        if (attempt == attempts - 1)
+            for (int r = 0; r < nrhs; ++r) h[r].status = WD_ERR_NOT_CONVERGED;
     }
+    WD_CUDA(c, cudaMemcpyAsync(x, xin, sfull, cudaMemcpyDeviceToDevice, c->stream));
+    WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->launches = launches;
 
     wd_status worst = WD_OK;
     for (int r = 0; r < nrhs; ++r) {
-        res[r].iters = h[r].iter;
-        res[r].reliable_updates = h[r].reliable;
+        res[r].iters = iters[r];
+        res[r].reliable_updates = reliable[r];
         res[r].true_rel_resid = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
         res[r].true_rel_resid_b = h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2);
-        res[r].seconds = ms * 1e-3;
+        res[r].seconds = ms_total * 1e-3;
         res[r].status = h[r].status;
         if (h[r].status != WD_OK && worst == WD_OK) worst = (wd_status)h[r].status;
     }
