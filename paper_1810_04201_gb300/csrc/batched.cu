@@ -134,7 +134,10 @@ __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
 }
 
 template <int SP, int RECON>
-__global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
+#ifndef WD_BATCH_MIN_BLOCKS
+#define WD_BATCH_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kTile, WD_BATCH_MIN_BLOCKS) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
     auto all = [](const Scalars &) { return 1; };
     auto active = [](const Scalars &c) { return c.active; };

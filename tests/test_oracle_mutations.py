@@ -83,7 +83,7 @@ def rel(a, b):
 
 
 def pins_pass(lib):
-    """True when every pin holds for this build of the oracle."""
+    """True when every pin holds for this compiled copy of the oracle."""
     from test_oracle_pins import paper_gammas
     g = paper_gammas()
     out = np.zeros(32)
