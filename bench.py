@@ -240,6 +240,7 @@ def config_of(args, w):
                         f"1e-10, inner precision {args.inner or w['inner']}, recon {args.recon}",
             "lattice": list(w["dims"]), "nrhs": w["nrhs"], "kappa": w["kappa"], "tol": 1e-10,
             "inner_prec": args.inner or w["inner"], "recon": args.recon,
+            "preconditioner": "even-odd" if getattr(args, "eo", False) else "none",
             "l2": "flushed (512 MB write) before every timed step and every timed Dslash launch",
             "parallelism": "replicas (one independent lattice per GPU)"}
 
@@ -255,6 +256,7 @@ def main():
     ap.add_argument("--recon", type=int, default=18, choices=[18, 12])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
+    ap.add_argument("--eo", action="store_true", help="even-odd preconditioned solve")
     ap.add_argument("--sweep", action="store_true", help="also time the Dslash at 8^4, 12^4, 16^4, 24^4")
     ap.add_argument("--dslash-only", default=None, metavar="LX,LY,LZ,LT",
                     help="time only the Dslash kernel on this lattice (profiling helper)")
@@ -310,7 +312,8 @@ def main():
 
     def solve():
         fx.zero_()
-        res, st = lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=wd.PRECS[inner], nrhs=nrhs, raise_on_fail=False)
+        res, st = lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=wd.PRECS[inner], nrhs=nrhs, raise_on_fail=False,
+                         delta=args.delta, precondition=1 if args.eo else 0)
         return res, st
 
     for _ in range(args.warmup):

@@ -134,10 +134,7 @@ __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
 }
 
 template <int SP, int RECON>
-#ifndef WD_BATCH_MIN_BLOCKS
-#define WD_BATCH_MIN_BLOCKS 3
-#endif
-__global__ void __launch_bounds__(kTile, WD_BATCH_MIN_BLOCKS) k_batched_cg(BatchArgs a) {
+__global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
     auto all = [](const Scalars &) { return 1; };
     auto active = [](const Scalars &c) { return c.active; };
@@ -389,8 +386,10 @@ __global__ void __launch_bounds__(kTile, WD_BATCH_MIN_BLOCKS) k_batched_cg(Batch
     });
 }
 
+// One persistent cooperative launch, captured once into a CUDA graph per argument
+// set (the arguments are pointers into context workspace, stable across calls).
 template <int SP, int RECON>
-static cudaError_t launch_batched(BatchArgs &a, cudaStream_t st, int *grid_out) {
+static cudaError_t build_batched(BatchArgs &a, cudaGraphExec_t *exec) {
     auto k = k_batched_cg<SP, RECON>;
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTile, 0);
@@ -400,18 +399,16 @@ static cudaError_t launch_batched(BatchArgs &a, cudaStream_t st, int *grid_out) 
     int grid = per_sm * sms;
     if (grid > a.ntiles) grid = a.ntiles;
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    *grid_out = grid;
-    // one persistent cooperative launch, captured in a CUDA graph
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kTile);
     cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // the legacy default stream cannot be captured: capture on a private stream
     cudaStream_t cap;
     e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -425,12 +422,8 @@ static cudaError_t launch_batched(BatchArgs &a, cudaStream_t st, int *grid_out) 
     }
     cudaStreamDestroy(cap);
     if (e != cudaSuccess) return e;
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return e;
-    e = cudaGraphLaunch(exec, st);
-    cudaGraphExecDestroy(exec);
     return e;
 }
 
@@ -530,15 +523,25 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     // about one second at GB300 clocks; a tenth of that for the stalled-wait test
     a.spin_limit = a.stall_test ? 200000000ll : 2000000000ll;
 
+    char key[160];
+    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p|%p", (int)sp, c0->recon, n, ntiles, prm->max_iter,
+             a.stall_test, d_part, d_lat);
+    cudaGraphExec_t exec;
+    auto it = c0->graphs.find(key);
+    if (it != c0->graphs.end()) {
+        exec = (cudaGraphExec_t)it->second;
+    } else {
+        cudaError_t e;
+        if (c0->recon == 12) e = sp == F32 ? build_batched<F32, 12>(a, &exec) : build_batched<F16, 12>(a, &exec);
+        else e = sp == F32 ? build_batched<F32, 18>(a, &exec) : build_batched<F16, 18>(a, &exec);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "building the batched persistent CG graph");
+        c0->graphs[key] = exec;
+    }
     cudaEvent_t e0, e1;
     WD_CUDA(c0, cudaEventCreate(&e0));
     WD_CUDA(c0, cudaEventCreate(&e1));
     WD_CUDA(c0, cudaEventRecord(e0, st));
-    int grid = 0;
-    cudaError_t e;
-    if (c0->recon == 12) e = sp == F32 ? launch_batched<F32, 12>(a, st, &grid) : launch_batched<F16, 12>(a, st, &grid);
-    else e = sp == F32 ? launch_batched<F32, 18>(a, st, &grid) : launch_batched<F16, 18>(a, st, &grid);
-    if (e != cudaSuccess) return cuda_fail(c0, e, "batched persistent CG launch");
+    WD_CUDA(c0, cudaGraphLaunch(exec, st));
     WD_CUDA(c0, cudaEventRecord(e1, st));
     for (int i = 0; i < n; ++i)
         WD_CUDA(c0, cudaMemcpyAsync(x[i], lat[i].x, spinor_bytes(F64, lat[i].g.Vs), cudaMemcpyDeviceToDevice, st));
