@@ -55,9 +55,9 @@ wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rh
 
     const int sts[] = {16, 32, 64, 128, 256};
     const int rts[] = {1, 2, 3, 4, 6, 8, 12, 16};
-    cudaEvent_t e0, e1;
-    WD_CUDA(c, cudaEventCreate(&e0));
-    WD_CUDA(c, cudaEventCreate(&e1));
+    EventPair ev;
+    WD_CUDA(c, ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     float best = 1e30f;
     DslashTiles bt = tiles_for(c, (Prec)prec, nrhs);
     for (int st : sts)
@@ -79,8 +79,6 @@ wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rh
                 bt = t;
             }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->tiles[(int)prec * 64 + nrhs] = bt;
     if (site_tile) *site_tile = bt.site_tile;
     if (rhs_tile) *rhs_tile = bt.rhs_tile;

@@ -537,9 +537,9 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
         if (e != cudaSuccess) return cuda_fail(c0, e, "building the batched persistent CG graph");
         c0->graphs[key] = exec;
     }
-    cudaEvent_t e0, e1;
-    WD_CUDA(c0, cudaEventCreate(&e0));
-    WD_CUDA(c0, cudaEventCreate(&e1));
+    EventPair ev;
+    WD_CUDA(c0, ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     WD_CUDA(c0, cudaEventRecord(e0, st));
     WD_CUDA(c0, cudaGraphLaunch(exec, st));
     WD_CUDA(c0, cudaEventRecord(e1, st));
@@ -551,8 +551,6 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     WD_CUDA(c0, cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c0->launches = 1;
     wd_status worst = WD_OK;
     for (int i = 0; i < n; ++i) {

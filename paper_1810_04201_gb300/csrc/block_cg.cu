@@ -273,7 +273,8 @@ static void record_block(wd_ctx *c, double kappa, int k, const void *g64, const 
     // (site tile x k) blocks: 16 sites when 16k is a multiple of 32, else 32 (<= 512 threads)
     const int st = (16 * k) % 32 == 0 ? 16 : 32;
     const int tiles = (c->g.V + st - 1) / st;
-    const dim3 blk(st, k), ggrid(tiles < 2 * 152 ? tiles : 2 * 152), mgrid(tiles);
+    const int gcap = 2 * num_sms();  // Gram kernels: at most two blocks per SM, one partial each
+    const dim3 blk(st, k), ggrid(tiles < gcap ? tiles : gcap), mgrid(tiles);
     {
         GraphBuilder gb(&plan.setup);
         DslashArgs a = base;
@@ -403,9 +404,9 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
     WD_CUDA(c, cudaMemcpyAsync(bs, &hb, sizeof hb, cudaMemcpyHostToDevice, c->stream));
     WD_CUDA(c, cudaMemcpyAsync(B, b, fk, cudaMemcpyDeviceToDevice, c->stream));
     WD_CUDA(c, cudaMemcpyAsync(X, x, fk, cudaMemcpyDeviceToDevice, c->stream));
-    cudaEvent_t e0, e1;
-    WD_CUDA(c, cudaEventCreate(&e0));
-    WD_CUDA(c, cudaEventCreate(&e1));
+    EventPair ev;
+    WD_CUDA(c, ev.create());
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     WD_CUDA(c, cudaEventRecord(e0, c->stream));
     WD_CUDA(c, cudaGraphLaunch(exec, c->stream));
     WD_CUDA(c, cudaEventRecord(e1, c->stream));
@@ -415,8 +416,6 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
     WD_CUDA(c, cudaStreamSynchronize(c->stream));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     const std::vector<long long> &cnt = c->graph_info[key];
     c->launches = cnt[0] + (long long)((hb.iter + 1) / 2 + 1) * cnt[1] + cnt[3];
     wd_status worst = WD_OK;

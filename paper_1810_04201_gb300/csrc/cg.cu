@@ -434,9 +434,9 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         }
         WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
         WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
-        cudaEvent_t e0, e1;
-        WD_CUDA(c, cudaEventCreate(&e0));
-        WD_CUDA(c, cudaEventCreate(&e1));
+        EventPair ev;
+        WD_CUDA(c, ev.create());
+        cudaEvent_t e0 = ev.e0, e1 = ev.e1;
         WD_CUDA(c, cudaEventRecord(e0, c->stream));
         long long host_launched = 0;
         if (host_loop) WD_CUDA(c, run_host_loop(c, hplan, f, nrhs, h[0].max_iter, &host_launched));
@@ -448,8 +448,6 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         WD_CUDA(c, cudaStreamSynchronize(c->stream));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         ms_total += ms;
         if (host_loop) {
             launches += host_launched;

@@ -18,6 +18,24 @@ wd_status cuda_fail(wd_ctx *c, cudaError_t e, const char *where);
         if (e_ != cudaSuccess) return ::wd::cuda_fail(ctx, e_, #call); \
     } while (0)
 
+// A pair of CUDA events released on every return path.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&e0);
+        return e == cudaSuccess ? cudaEventCreate(&e1) : e;
+    }
+    float ms() const {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        return t;
+    }
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // workspace: named device buffer of at least `bytes` (kept across calls)
 wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);
 // device gauge field of precision p at the context's recon (created on first use)

@@ -275,3 +275,36 @@ def test_even_odd_rejects_odd_extents(wd):
     b = lat.pack(gen.gaussian_source((3, 4, 4, 4), 1))
     res, st = lat.cg(0.12, b, lat.new_field(), precondition=1, raise_on_fail=False)
     assert st == 1
+
+
+def test_max_rhs_and_side_stream(wd):
+    """16 right-hand sides (the maximum) on a non-default stream."""
+    import torch
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=23)
+    B = gen.gaussian_source(dims, seed=24, nrhs=16)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        lat = wd.Lattice(dims)
+        lat.set_gauge(U)
+        fb, fx = lat.pack(B), lat.new_field(nrhs=16)
+        res, st = lat.cg(kappa, fb, fx, tol=1e-10, nrhs=16, inner=1)
+        X = lat.unpack(fx, nrhs=16, squeeze=False)
+    assert st == 0 and all(r["true_rel_resid"] <= 1e-10 for r in res)
+    for j in (0, 15):
+        x_ref, _ = ref_solution(U, B[j], kappa, dims)
+        assert oracle.rel_err(X[j], x_ref) < 1e-9
+    with pytest.raises(wd.WDError):
+        lat.cg(kappa, fb, fx, nrhs=17)
+
+
+def test_canonical_pageable_host_buffers(wd):
+    dims, kappa = (4, 4, 2, 4), 0.12
+    U = gen.haar_links(dims, seed=25)
+    b = gen.gaussian_source(dims, seed=26)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    x = np.zeros_like(b)
+    res, st = lat.cg_canonical(kappa, b, x, tol=1e-10, precondition=1)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    assert st == 0 and oracle.rel_err(x, x_ref) < 1e-9
