@@ -41,8 +41,9 @@ FLOP_PER_SITE = 1320
 # Algorithmic bytes per site of one Dslash (each input field read once, output
 # written once): spinor in + links + spinor out.
 SPINOR_BYTES = {"f64": 192, "f32": 96, "f16": 52, "df32": 192}
-LINK_BYTES = {("f64", 18): 576, ("f64", 12): 384, ("f32", 18): 288, ("f32", 12): 192, ("f16", 18): 144,
-              ("f16", 12): 96, ("df32", 18): 576, ("df32", 12): 384}
+LINK_BYTES = {("f64", 18): 576, ("f64", 12): 384, ("f64", 8): 256, ("f32", 18): 288, ("f32", 12): 192,
+              ("f32", 8): 128, ("f16", 18): 144, ("f16", 12): 96, ("f16", 8): 64, ("df32", 18): 576,
+              ("df32", 12): 384, ("df32", 8): 256}
 PREC_ID = {"f64": 0, "f32": 1, "f16": 2, "df32": 3}
 WORKLOADS = {
     "c1": dict(dims=(4, 4, 4, 4), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=1),
@@ -253,7 +254,7 @@ def main():
     ap.add_argument("--impl", default="wd", choices=["wd", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5"])
     ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16", "df32"])
-    ap.add_argument("--recon", type=int, default=18, choices=[18, 12])
+    ap.add_argument("--recon", type=int, default=18, choices=[18, 12, 8])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eo", action="store_true", help="even-odd preconditioned solve")

@@ -96,8 +96,12 @@ wd_status wd_set_stream(wd_ctx *ctx, void *stream);
  * U_canon: canonical links (4*V*9 complex128), host memory (on_device = 0) or device
  * memory (on_device = 1).  recon = 18 stores all nine entries; recon = 12 stores the
  * first two rows and rebuilds the third as conj(row0 x row1) (section 6.1, valid for
- * SU(3) links only).  The lower-precision copies used by WD_F32/WD_F16 operators are
- * derived from the same field when first needed. */
+ * SU(3) links only); recon = 8 stores U01, U02, U10 and the phases of U00 and U20 and
+ * rebuilds the rest from unitarity and det U = 1 (the reconstruction the paper defers
+ * in section 6.1; SU(3) links with |U01|^2 + |U02|^2 >= 1e-6 on every link, so not the
+ * unit gauge: otherwise WD_ERR_ARG, and the context holds no gauge field until the
+ * next successful call).  The lower-precision copies used by WD_F32/WD_F16/WD_DF32
+ * operators are derived from the same field when first needed. */
 wd_status wd_set_gauge(wd_ctx *ctx, const double *U_canon, int on_device, int recon);
 
 /* Bytes of one device field of nrhs right-hand sides in precision prec. */
@@ -229,7 +233,10 @@ wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const v
  * the fastest for later calls.  Writes the choice to *site_tile and *rhs_tile
  * (either may be NULL).  Uses context-owned scratch fields; synchronises the stream. */
 wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
-/* Fix the tile choice by hand (site_tile in {32, 64, 128, 256}; rhs_tile >= 1). */
+/* Fix the tile choice by hand: site_tile in {16, 32, 64, 128, 256} threads,
+ * 1 <= rhs_tile <= nrhs, site_tile * rhs_tile <= 256 and a multiple of 32.  WD_F64
+ * runs each site on two lanes (site_tile / 2 sites per block) and needs
+ * site_tile >= 32.  Unsupported shapes: WD_ERR_ARG. */
 wd_status wd_set_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int site_tile, int rhs_tile);
 
 /* Launch-configuration query: number of kernel launches the last wd_* call queued

@@ -1,4 +1,5 @@
 // C ABI of libwd: contexts, gauge upload, pack/unpack and the plain operators.
+#include <algorithm>
 #include <cstring>
 #include <cmath>
 #include "dslash.cuh"
@@ -56,17 +57,13 @@ wd_status gauge_get(wd_ctx *c, Prec p, const void **out) {
         void *d = nullptr;
         WD_CUDA(c, cudaMalloc(&d, gauge_bytes(p, c->recon, c->g.Vs)));
         const size_t dir = gauge_dir_bytes(c, p);
-        if (c->recon == 12) {
-            if (p == F64) gauge_pack<F64, 12>(c->gauge_canon, d, c->g, dir, c->stream);
-            else if (p == F32) gauge_pack<F32, 12>(c->gauge_canon, d, c->g, dir, c->stream);
-            else if (p == DF32) gauge_pack<DF32, 12>(c->gauge_canon, d, c->g, dir, c->stream);
-            else gauge_pack<F16, 12>(c->gauge_canon, d, c->g, dir, c->stream);
-        } else {
-            if (p == F64) gauge_pack<F64, 18>(c->gauge_canon, d, c->g, dir, c->stream);
-            else if (p == F32) gauge_pack<F32, 18>(c->gauge_canon, d, c->g, dir, c->stream);
-            else if (p == DF32) gauge_pack<DF32, 18>(c->gauge_canon, d, c->g, dir, c->stream);
-            else gauge_pack<F16, 18>(c->gauge_canon, d, c->g, dir, c->stream);
-        }
+        with_recon(c->recon, [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            if (p == F64) gauge_pack<F64, R>(c->gauge_canon, d, c->g, dir, c->stream);
+            else if (p == F32) gauge_pack<F32, R>(c->gauge_canon, d, c->g, dir, c->stream);
+            else if (p == DF32) gauge_pack<DF32, R>(c->gauge_canon, d, c->g, dir, c->stream);
+            else gauge_pack<F16, R>(c->gauge_canon, d, c->g, dir, c->stream);
+        });
         WD_CUDA(c, cudaGetLastError());
         c->launches += 1;
         c->gauge[p] = d;
@@ -96,17 +93,13 @@ wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes) {
     if (!c->gauge_eo[p]) {
         void *d = nullptr;
         WD_CUDA(c, cudaMalloc(&d, 8 * dir));
-        if (c->recon == 12) {
-            if (p == F64) gauge_pack_eo<F64, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else if (p == F32) gauge_pack_eo<F32, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else if (p == DF32) gauge_pack_eo<DF32, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else gauge_pack_eo<F16, 12>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-        } else {
-            if (p == F64) gauge_pack_eo<F64, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else if (p == F32) gauge_pack_eo<F32, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else if (p == DF32) gauge_pack_eo<DF32, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-            else gauge_pack_eo<F16, 18>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
-        }
+        with_recon(c->recon, [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            if (p == F64) gauge_pack_eo<F64, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == F32) gauge_pack_eo<F32, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else if (p == DF32) gauge_pack_eo<DF32, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+            else gauge_pack_eo<F16, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
+        });
         WD_CUDA(c, cudaGetLastError());
         c->launches += 1;
         c->gauge_eo[p] = d;
@@ -204,7 +197,7 @@ wd_status wd_set_stream(wd_ctx *c, void *stream) {
 wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     if (!c) return WD_ERR_ARG;
     if (!U) return fail(c, WD_ERR_ARG, "wd_set_gauge: null gauge pointer");
-    if (recon != 18 && recon != 12) return fail(c, WD_ERR_ARG, "wd_set_gauge: recon must be 18 or 12");
+    if (recon != 18 && recon != 12 && recon != 8) return fail(c, WD_ERR_ARG, "wd_set_gauge: recon must be 18, 12 or 8");
     const size_t bytes = (size_t)4 * c->g.V * 9 * 16;
     WD_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int p = 0; p < kNumPrec; ++p) {
@@ -221,10 +214,31 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     WD_CUDA(c, cudaMemcpyAsync(c->gauge_canon, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                c->stream));
     c->recon = recon;
-    c->has_gauge = true;
+    c->has_gauge = false;
     // graphs bake gauge pointers in
     for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
     c->graphs.clear();
+    if (recon == 8) {
+        // the 8-real parametrisation divides by |u01|^2 + |u02|^2 (zero for the unit link)
+        void *w;
+        wd_status s = ws_get(c, "gauge_check", sizeof(unsigned), &w);
+        if (s != WD_OK) return s;
+        WD_CUDA(c, cudaMemsetAsync(w, 0x7f, sizeof(unsigned), c->stream));
+        const size_t nl = (size_t)4 * c->g.V;
+        k_gauge_min_offdiag<<<(int)std::min<size_t>((nl + 255) / 256, 4096), 256, 0, c->stream>>>(
+            reinterpret_cast<const double2 *>(c->gauge_canon), nl, static_cast<unsigned *>(w));
+        WD_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+        unsigned bits = 0;
+        WD_CUDA(c, cudaMemcpyAsync(&bits, w, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+        WD_CUDA(c, cudaStreamSynchronize(c->stream));
+        float nmin;
+        std::memcpy(&nmin, &bits, sizeof nmin);
+        if (!(nmin >= 1e-6f))
+            return fail(c, WD_ERR_ARG, "wd_set_gauge: recon 8 needs |U01|^2 + |U02|^2 >= 1e-6 on every link "
+                                       "(smallest: " + std::to_string(nmin) + "); use recon 12 or 18");
+    }
+    c->has_gauge = true;
     const void *d;
     wd_status s = gauge_get(c, F64, &d);
     if (s != WD_OK) return s;

@@ -531,9 +531,10 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     if (it != c0->graphs.end()) {
         exec = (cudaGraphExec_t)it->second;
     } else {
-        cudaError_t e;
-        if (c0->recon == 12) e = sp == F32 ? build_batched<F32, 12>(a, &exec) : build_batched<F16, 12>(a, &exec);
-        else e = sp == F32 ? build_batched<F32, 18>(a, &exec) : build_batched<F16, 18>(a, &exec);
+        const cudaError_t e = with_recon(c0->recon, [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            return sp == F32 ? build_batched<F32, R>(a, &exec) : build_batched<F16, R>(a, &exec);
+        });
         if (e != cudaSuccess) return cuda_fail(c0, e, "building the batched persistent CG graph");
         c0->graphs[key] = exec;
     }

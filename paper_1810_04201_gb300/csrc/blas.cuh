@@ -133,6 +133,33 @@ template <int P> __global__ void k_zero(VecArgs v) {
 // at index idx of arrays with stride Vs starting at `base` (one direction).
 template <int P, int RECON>
 __device__ __forceinline__ void pack_link(const double2 *u, char *base, int Vs, int idx) {
+    if constexpr (RECON == 8) {
+        // entries 1, 2, 3 and the phases of entries 0 and 6
+        const double th0 = atan2(u[0].y, u[0].x), th6 = atan2(u[6].y, u[6].x);
+        if (P == F64) {
+            double2 *d = reinterpret_cast<double2 *>(base) + idx;
+            for (int e = 0; e < 3; ++e) d[(size_t)e * Vs] = u[e + 1];
+            d[(size_t)3 * Vs] = make_double2(th0, th6);
+        } else if (P == DF32) {
+            float4 *d = reinterpret_cast<float4 *>(base) + idx;
+            for (int e = 0; e < 3; ++e) {
+                const df re(u[e + 1].x), im(u[e + 1].y);
+                d[(size_t)e * Vs] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+            const df t0(th0), t6(th6);
+            d[(size_t)3 * Vs] = make_float4(t0.hi, t0.lo, t6.hi, t6.lo);
+        } else if (P == F32) {
+            float4 *d = reinterpret_cast<float4 *>(base) + idx;
+            d[0] = make_float4((float)u[1].x, (float)u[1].y, (float)u[2].x, (float)u[2].y);
+            d[Vs] = make_float4((float)u[3].x, (float)u[3].y, (float)th0, (float)th6);
+        } else {
+            const double ipi = 0.31830988618379067;  // 1 / pi
+            uint4 *d = reinterpret_cast<uint4 *>(base) + idx;
+            *d = make_uint4(f2h((float)u[1].x, (float)u[1].y), f2h((float)u[2].x, (float)u[2].y),
+                            f2h((float)u[3].x, (float)u[3].y), f2h((float)(th0 * ipi), (float)(th6 * ipi)));
+        }
+        return;
+    }
     constexpr int n = RECON == 12 ? 6 : 9;
     if (P == F64) {
         double2 *d = reinterpret_cast<double2 *>(base) + idx;
@@ -174,6 +201,18 @@ template <int P, int RECON> __global__ void k_gauge_pack(const double2 *canon, v
     const int s = blockIdx.x * blockDim.x + threadIdx.x, mu = blockIdx.y;
     if (s >= V) return;
     pack_link<P, RECON>(canon + ((size_t)mu * V + s) * 9, reinterpret_cast<char *>(dst) + (size_t)mu * dir_bytes, Vs, s);
+}
+
+// smallest n = |u01|^2 + |u02|^2 over all links (the recon-8 denominator), as the
+// bits of a non-negative float (ordered like the floats); *out starts above any n
+template <int DUMMY = 0> __global__ void k_gauge_min_offdiag(const double2 *canon, size_t nlinks, unsigned *out) {
+    float m = 3.0e38f;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += (size_t)gridDim.x * blockDim.x) {
+        const double2 a1 = canon[l * 9 + 1], a2 = canon[l * 9 + 2];
+        m = fminf(m, (float)(a1.x * a1.x + a1.y * a1.y + a2.x * a2.x + a2.y * a2.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, __float_as_uint(m));
 }
 
 // gauge in checkerboard order: U_mu(n) -> parity of n, index n / 2 (arrays of stride Vhs)

@@ -343,7 +343,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
     f.sc = (Scalars *)tmp;
     if ((s = ws_get(c, "bk_state", sizeof(BlockState), &tmp)) != WD_OK) return s;
     f.bs = (BlockState *)tmp;
-    const size_t npart = (size_t)WD_MAX_RHS * 3 * 8192;
+    const size_t npart = (size_t)WD_MAX_RHS * 3 * kMaxPartialBlocks;
     if ((s = ws_get(c, "partial", npart * sizeof(double), &tmp)) != WD_OK) return s;
     f.partial = (double *)tmp;
     if ((s = ws_get(c, "counter", 256, &tmp)) != WD_OK) return s;
@@ -366,8 +366,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
         cudaGraphConditionalHandle hw = 0;
         cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault);
         Plan plan;
-        if (c->recon == 12) record_block<12>(c, kappa, k, g64, f, hw, plan);
-        else record_block<18>(c, kappa, k, g64, f, hw, plan);
+        with_recon(c->recon, [&](auto rc) { record_block<decltype(rc)::value>(c, kappa, k, g64, f, hw, plan); });
         std::vector<cudaGraphNode_t> deps;
         if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
         cudaGraph_t body = nullptr;

@@ -1,0 +1,263 @@
+// Solver plans of the device-resident CG (section 2.2): the recording of every
+// kernel of one solve for a given link compression, inner precision, normal form
+// and preconditioning, and its assembly into a CUDA graph with device-side loop.
+// Each link compression is instantiated in its own translation unit
+// (cg_recon18.cu, cg_recon12.cu, cg_recon8.cu), which keeps the build parallel.
+#pragma once
+#include <vector>
+#include "cg_kernels.cuh"
+#include "plan.cuh"
+#include "wd_host.h"
+
+namespace wd {
+
+// Record the FP64 (inner == F64) or mixed-precision solver.  hwhile / hif are the
+// conditional handles the loop kernels set (0 for the host-driven loop).
+// NE = false: CGNR, A = D^dag D, rhs D^dag b.  NE = true: CGNE, the paper's form
+// (section 2.2): A = D D^dag, rhs b, iterate y (kept in the x field), x = D^dag y.
+// The two share every kernel; only which of D and D^dag comes first changes.
+// EO = true: even-odd preconditioning; the iteration runs on the even half with
+// the Schur operator, the odd half is rebuilt at the end (CGNR only).
+template <int RECON, int SP, bool NE, bool EO>
+static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                        cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif, Plan &plan) {
+    static_assert(!(NE && EO), "even-odd preconditioning is built for CGNR");
+    GraphBuilder gb(&plan.setup);
+    const Geom gw = EO ? f.eo.ge : c->g;  // geometry of the iterated fields
+    const size_t s64 = spinor_bytes(F64, gw.Vs), sin = spinor_bytes((Prec)SP, gw.Vs), s32 = spinor_bytes(F32, gw.Vs);
+    const bool mixed = SP != F64;
+
+    DslashArgs base{};
+    base.g = gw;
+    base.gauge = g64;
+    base.gauge_dir = gauge_dir_bytes(c, F64);
+    base.kappa = pl.kappa;
+    base.nrhs = pl.nrhs;
+    base.sc = f.sc;
+    base.partial = f.partial;
+    base.counter = f.counter;
+    base.state = f.state;
+    base.in_stride = base.out_stride = base.a0_stride = base.a1_stride = base.a2_stride = base.a3_stride = s64;
+
+    VecArgs vb{};
+    vb.V = gw.V;
+    vb.Vs = gw.Vs;
+    vb.nrhs = pl.nrhs;
+    vb.sc = f.sc;
+    vb.state = f.state;
+
+    // first (OP1) and second (OP2) operator of A: CGNR D then D^dag, CGNE D^dag then D
+    constexpr bool OP1 = NE, OP2 = !NE;
+    const size_t sfull = spinor_bytes(F64, c->g.Vs);
+    if constexpr (EO) {
+        // split b and x0 into halves; the Schur right-hand side b^ = b_e + kappa H_eo b_o
+        VecArgs v = vb;
+        v.V = c->g.V;
+        v.Vs = c->g.Vs;
+        v.mask = 0;
+        v.a = f.eo.bfull; v.a_stride = sfull; v.b = f.eo.be; v.c = f.eo.bo; v.b_stride = s64;
+        gb.kernel(k_split_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        v.a = f.eo.xfull; v.b = f.x; v.c = f.eo.xo;
+        gb.kernel(k_split_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        DslashArgs a = base;
+        a.mask = 0;
+        a.g = f.eo.ge;
+        a.gauge = f.eo.gauge[F64];
+        a.gauge_dir = f.eo.gdir[F64];
+        a.in = f.eo.bo; a.xsrc = f.eo.be; a.xsrc_stride = s64; a.out = f.b;
+        a.kappa = -pl.kappa;
+        add_dslash<F64, RECON, false, EpXpay, true>(gb, a, pl.t64, false);
+    }
+    // ---- setup (FP64): db = rhs; t = OP1 x0; r = db - OP2 t; p = r
+    {
+        DslashArgs a = base;
+        a.mask = 0;
+        a.in = f.b; a.out = f.db;
+        if (NE) a.kappa = 0.0;  // D with kappa = 0 is the identity: db = b, |b|^2
+        add_op<F64, RECON, true, EpSetupDb, EO>(gb, a, pl.t64, true, f);
+        a.kappa = pl.kappa;
+        a.in = f.x; a.out = f.t;
+        add_op<F64, RECON, OP1, EpXpay, EO>(gb, a, pl.t64, false, f);
+        a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
+        add_op<F64, RECON, OP2, EpSetupR, EO>(gb, a, pl.t64, true, f);
+    }
+    if (mixed) {
+        VecArgs v = vb;
+        v.mask = 0;
+        v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
+        add_vec(gb, k_convert<F64, SP>, v);
+        v.b = f.ps;
+        add_vec(gb, k_convert<F64, SP>, v);
+        v.b = f.xs; v.b_stride = s32;
+        add_vec(gb, k_zero<F32>, v);
+    }
+
+    // ---- loop
+    {
+        GraphBuilder bb(&plan.pre);
+        if (!mixed) {
+            DslashArgs a = base;
+            a.mask = 1;
+            a.in = f.p; a.out = f.t;
+            add_op<F64, RECON, OP1, EpCG1, EO>(bb, a, pl.t64, true, f);
+            a.in = f.t; a.a0 = f.p; a.a1 = f.r; a.a2 = f.x;
+            add_op<F64, RECON, OP2, EpCG2, EO>(bb, a, pl.t64, true, f);
+            VecArgs v = vb;
+            v.mask = 1;
+            v.a = f.r; v.a_stride = s64; v.b = f.p; v.b_stride = s64; v.cond = hwhile;
+            add_vec(bb, k_xpby<F64>, v);
+        } else {
+            DslashArgs a = base;
+            a.mask = 1;
+            a.gauge = gin;
+            a.gauge_dir = gauge_dir_bytes(c, (Prec)SP);
+            a.in_stride = a.out_stride = a.a0_stride = a.a1_stride = sin;
+            a.a2_stride = s32;
+            a.in = f.ps; a.out = f.ts;
+            add_op<SP, RECON, OP1, EpCG1, EO>(bb, a, pl.tin, true, f);
+            a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
+            add_op<SP, RECON, OP2, EpCG2Mixed, EO>(bb, a, pl.tin, true, f);
+            plan.has_if = true;
+            {
+                GraphBuilder ib(&plan.ifb);
+                VecArgs v = vb;
+                v.mask = 2;
+                v.a = f.xs; v.a_stride = s32; v.b = f.x; v.b_stride = s64;
+                add_vec(ib, k_reliable_x<0>, v);
+                DslashArgs r = base;
+                r.mask = 2;
+                r.in = f.x; r.out = f.t;
+                add_op<F64, RECON, OP1, EpXpay, EO>(ib, r, pl.t64, false, f);
+                r.in = f.t; r.a0 = f.db; r.a1 = f.r;
+                add_op<F64, RECON, OP2, EpReliable, EO>(ib, r, pl.t64, true, f);
+                v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
+                add_vec(ib, k_convert<F64, SP>, v);
+            }
+            bb.cur = &plan.post;
+            VecArgs v = vb;
+            v.mask = 1;
+            v.a = f.rs; v.a_stride = sin; v.b = f.ps; v.b_stride = sin; v.cond = hwhile;
+            add_vec(bb, k_xpby<SP>, v);
+        }
+    }
+
+    // ---- final FP64 check: t = D x, |b - t|^2; |D^dag b - D^dag t|^2 (full lattice)
+    gb.cur = &plan.fin;
+    DslashArgs a = base;
+    a.mask = 0;
+    void *xf = f.x, *bf = f.b, *tf = f.t, *dbt = f.db;
+    if constexpr (EO) {
+        // x_o = b_o + kappa H_oe x_e, join the halves, then check on the full lattice
+        DslashArgs o = base;
+        o.mask = 0;
+        o.g = f.eo.go;
+        o.gauge = f.eo.gauge[F64];
+        o.gauge_dir = f.eo.gdir[F64];
+        o.in = f.x; o.xsrc = f.eo.bo; o.xsrc_stride = s64; o.out = f.eo.xo;
+        o.kappa = -pl.kappa;
+        add_dslash<F64, RECON, false, EpXpay, true>(gb, o, pl.t64, false);
+        VecArgs v = vb;
+        v.V = c->g.V;
+        v.Vs = c->g.Vs;
+        v.mask = 0;
+        v.a = f.x; v.c = f.eo.xo; v.a_stride = s64; v.b = f.eo.xfull; v.b_stride = sfull;
+        gb.kernel(k_join_eo<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), EoVecArgs{v, gw.Vs, c->g});
+        a.g = c->g;
+        a.gauge = g64;
+        a.gauge_dir = gauge_dir_bytes(c, F64);
+        a.in_stride = a.out_stride = a.a0_stride = sfull;
+        xf = f.eo.xfull; bf = f.eo.bfull; tf = f.eo.tfull; dbt = f.eo.dbfull;
+        a.in = bf; a.out = dbt;
+        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+    }
+    if (NE) {
+        // x = D^dag y ; D^dag b (into p) and its norm for the normal-equation residual
+        a.in = f.x; a.out = f.t;
+        add_dslash<F64, RECON, true, EpXpay>(gb, a, pl.t64, false);
+        VecArgs v = vb;
+        v.mask = 0;
+        v.a = f.t; v.a_stride = s64; v.b = f.x; v.b_stride = s64;
+        add_vec(gb, k_convert<F64, F64>, v);
+        a.in = f.b; a.out = f.p;
+        add_dslash<F64, RECON, true, EpSetupDb>(gb, a, pl.t64, true);
+        dbt = f.p;
+    }
+    a.in = xf; a.out = tf; a.a0 = bf;
+    add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
+    a.in = tf; a.a0 = dbt;
+    add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);
+}
+
+// One CUDA graph: setup -> WHILE { pre -> IF { ifb } -> post } -> final.
+template <int RECON, int SP, bool NE, bool EO>
+static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                               cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    cudaGraph_t graph;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle hwhile = 0, hif = 0;
+    e = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess && SP != F64) e = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
+    Plan plan;
+    if (e == cudaSuccess) record_plan<RECON, SP, NE, EO>(c, pl, f, g64, gin, hwhile, hif, plan);
+    std::vector<cudaGraphNode_t> deps;
+    if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) e = add_conditional(graph, deps, hwhile, cudaGraphCondTypeWhile, &body);
+    if (e == cudaSuccess) {
+        std::vector<cudaGraphNode_t> bd;
+        e = add_chain(body, bd, plan.pre);
+        if (e == cudaSuccess && plan.has_if) {
+            cudaGraph_t ifg = nullptr;
+            e = add_conditional(body, bd, hif, cudaGraphCondTypeIf, &ifg);
+            std::vector<cudaGraphNode_t> id;
+            if (e == cudaSuccess) e = add_chain(ifg, id, plan.ifb);
+        }
+        if (e == cudaSuccess) e = add_chain(body, bd, plan.post);
+    }
+    if (e == cudaSuccess) e = add_chain(graph, deps, plan.fin);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    counts = {(long long)plan.setup.size(), (long long)(plan.pre.size() + plan.post.size()),
+              (long long)plan.ifb.size(), (long long)plan.fin.size()};
+    return e;
+}
+
+template <int RECON, bool NE, bool EO>
+static cudaError_t build_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                                cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    switch (pl.inner) {
+    case F64: return build_graph<RECON, F64, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case F32: return build_graph<RECON, F32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case DF32: return build_graph<RECON, DF32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    default: return build_graph<RECON, F16, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    }
+}
+
+template <int RECON>
+cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                             cudaGraphExec_t *exec, std::vector<long long> &counts) {
+    if (pl.eo) return build_for_ne<RECON, false, true>(c, pl, f, g64, gin, exec, counts);
+    return pl.ne ? build_for_ne<RECON, true, false>(c, pl, f, g64, gin, exec, counts)
+                 : build_for_ne<RECON, false, false>(c, pl, f, g64, gin, exec, counts);
+}
+
+template <int RECON, bool NE, bool EO>
+static void record_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
+                          Plan &plan) {
+    switch (pl.inner) {
+    case F64: record_plan<RECON, F64, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F32: record_plan<RECON, F32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case DF32: record_plan<RECON, DF32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    default: record_plan<RECON, F16, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    }
+}
+
+template <int RECON>
+void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan) {
+    if (pl.eo) record_for_ne<RECON, false, true>(c, pl, f, g64, gin, plan);
+    else if (pl.ne) record_for_ne<RECON, true, false>(c, pl, f, g64, gin, plan);
+    else record_for_ne<RECON, false, false>(c, pl, f, g64, gin, plan);
+}
+
+}  // namespace wd

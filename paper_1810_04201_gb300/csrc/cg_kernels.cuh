@@ -44,23 +44,23 @@ __device__ __forceinline__ bool reduce_finish(const DslashArgs &a, double (&v)[N
 
 __device__ __forceinline__ bool is_fin(double x) { return isfinite(x); }
 
-template <class R> __device__ __forceinline__ void xpay_site(C<R> (&p)[12], const C<R> (&acc)[12], R k) {
+template <class R, int N> __device__ __forceinline__ void xpay_site(C<R> (&p)[N], const C<R> (&acc)[N], R k) {
 #pragma unroll
-    for (int c = 0; c < 12; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
+    for (int c = 0; c < N; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
 }
 
 // db = D^dag b (out); |db|^2 -> rhs2, |b|^2 -> b2, tol2 *= rhs2
 struct EpSetupDb {
     struct State { double v[2]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> p[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, p);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> p[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, p);
         st.v[1] += norm2_of(p);
         xpay_site(p, acc, R(a.kappa));
         st.v[0] += norm2_of(p);
-        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+        store_part<P>(pt, rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -76,18 +76,18 @@ struct EpSetupDb {
 // q = D^dag t; r = db - q (a1), p = r (a2); rho = |r|^2; rows already converged stop
 struct EpSetupR {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> q[12], d[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, q);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> q[Pt::N], d[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
         xpay_site(q, acc, R(a.kappa));
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        for (int c = 0; c < Pt::N; ++c) d[c] = csub(d[c], q[c]);
         st.v[0] += norm2_of(d);
-        SpinorIO<P>::store(rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
-        SpinorIO<P>::store(rhs_ptr<R>(a.a2, a.a2_stride, r), a.g.Vs, s, d);
+        store_part<P>(pt, rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
+        store_part<P>(pt, rhs_ptr<R>(a.a2, a.a2_stride, r), a.g.Vs, s, d);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -106,14 +106,14 @@ struct EpSetupR {
 // t = D p (out); pAp = |t|^2; alpha = rho / pAp
 struct EpCG1 {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> p[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, p);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> p[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, p);
         xpay_site(p, acc, R(a.kappa));
         st.v[0] += norm2_of(p);
-        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+        store_part<P>(pt, rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -130,25 +130,25 @@ struct EpCG1 {
 // FP64 step: q = D^dag t; r -= alpha q (a1); x += alpha p (a2, p = a0); rho' = |r|^2
 struct EpCG2 {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
         const R alpha = R(a.sc[r].alpha);
-        C<R> q[12], v[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        C<R> q[Pt::N], v[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
         xpay_site(q, acc, R(a.kappa));
         void *rr = rhs_ptr<R>(a.a1, a.a1_stride, r);
-        SpinorIO<P>::load(rr, a.g.Vs, s, v);
+        load_part<P>(pt, rr, a.g.Vs, s, v);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
+        for (int c = 0; c < Pt::N; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
         st.v[0] += norm2_of(v);
-        SpinorIO<P>::store(rr, a.g.Vs, s, v);
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
+        store_part<P>(pt, rr, a.g.Vs, s, v);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
         void *xr = rhs_ptr<R>(a.a2, a.a2_stride, r);
-        SpinorIO<P>::load(xr, a.g.Vs, s, v);
+        load_part<P>(pt, xr, a.g.Vs, s, v);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re + alpha * q[c].re, v[c].im + alpha * q[c].im};
-        SpinorIO<P>::store(xr, a.g.Vs, s, v);
+        for (int c = 0; c < Pt::N; ++c) v[c] = C<R>{v[c].re + alpha * q[c].re, v[c].im + alpha * q[c].im};
+        store_part<P>(pt, xr, a.g.Vs, s, v);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -171,27 +171,27 @@ struct EpCG2 {
 // if-condition (cond) when any row needs one.
 struct EpCG2Mixed {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
         const R alpha = R(a.sc[r].alpha);
-        C<R> q[12], v[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, q);
+        C<R> q[Pt::N], v[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
         xpay_site(q, acc, R(a.kappa));
         void *rr = rhs_ptr<R>(a.a1, a.a1_stride, r);
-        SpinorIO<P>::load(rr, a.g.Vs, s, v);
+        load_part<P>(pt, rr, a.g.Vs, s, v);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
+        for (int c = 0; c < Pt::N; ++c) v[c] = C<R>{v[c].re - alpha * q[c].re, v[c].im - alpha * q[c].im};
         st.v[0] += norm2_of(v);
-        SpinorIO<P>::store(rr, a.g.Vs, s, v);
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
-        C<float> xs[12];
+        store_part<P>(pt, rr, a.g.Vs, s, v);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, q);
+        C<float> xs[Pt::N];
         void *xr = rhs_ptr<R>(a.a2, a.a2_stride, r);
-        SpinorIO<F32>::load(xr, a.g.Vs, s, xs);
+        load_part<F32>(pt, xr, a.g.Vs, s, xs);
 #pragma unroll
-        for (int c = 0; c < 12; ++c)
+        for (int c = 0; c < Pt::N; ++c)
             xs[c] = C<float>{xs[c].re + float(alpha * q[c].re), xs[c].im + float(alpha * q[c].im)};
-        SpinorIO<F32>::store(xr, a.g.Vs, s, xs);
+        store_part<F32>(pt, xr, a.g.Vs, s, xs);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -222,17 +222,17 @@ struct EpCG2Mixed {
 // Reliable update, FP64: q = D^dag t (t = D x); r = db - q (a1, db = a0); rho = |r|^2
 struct EpReliable {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> q[12], d[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, q);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> q[Pt::N], d[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
         xpay_site(q, acc, R(a.kappa));
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        for (int c = 0; c < Pt::N; ++c) d[c] = csub(d[c], q[c]);
         st.v[0] += norm2_of(d);
-        SpinorIO<P>::store(rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
+        store_part<P>(pt, rhs_ptr<R>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
@@ -253,16 +253,16 @@ struct EpReliable {
 // Final check, pass 1: t = D x (out); |b - t|^2 -> true_b2 (b = a0)
 struct EpTrue1 {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> p[12], b[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, p);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> p[Pt::N], b[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, p);
         xpay_site(p, acc, R(a.kappa));
-        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, b);
+        store_part<P>(pt, rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, b);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) b[c] = csub(b[c], p[c]);
+        for (int c = 0; c < Pt::N; ++c) b[c] = csub(b[c], p[c]);
         st.v[0] += norm2_of(b);
     }
     template <int P>
@@ -274,15 +274,15 @@ struct EpTrue1 {
 // Final check, pass 2: q = D^dag t; |db - q|^2 -> true_n2 (db = a0)
 struct EpTrue2 {
     struct State { double v[1]; };
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &st) {
-        C<R> q[12], d[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, q);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        C<R> q[Pt::N], d[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
         xpay_site(q, acc, R(a.kappa));
-        SpinorIO<P>::load(rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
+        load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
+        for (int c = 0; c < Pt::N; ++c) d[c] = csub(d[c], q[c]);
         st.v[0] += norm2_of(d);
     }
     template <int P>

@@ -386,6 +386,241 @@ __device__ __forceinline__ void hopping_rolled_dir_eo(const Geom &g, const void 
     }
 }
 
+// ---------------------------------------------------------------- two lanes per site
+// FP64 is bound by the FP64 units, which belong to the four schedulers of an SM:
+// a scheduler without warps leaves its unit idle, as in the partial last wave of a
+// launch.  So FP64 sites run on two lanes of a warp, lane l and l ^ 16, and twice
+// as many warps share the work.  Lane half hh computes spin component hh of every
+// projected half spinor.  Row hh of A_mu has one entry f, in column ps - 2, where
+// ps = 3 - hh for mu = 0, 1 and ps = 2 + hh for mu = 2, 3, so
+//   h_hh = psi_hh + s f psi_ps,   upper spin hh += (U h)_hh,   lower spin ps += s conj(f) (U h)_hh,
+// with f = i (mu = 0), -1 / +1 (mu = 1, hh = 0 / 1), i / -i (mu = 2), 1 (mu = 3).
+// The two halves do exactly the arithmetic of one site between them.  The lane's
+// accumulator holds spin hh [0..2], spin 3 - hh [3..5] (from mu = 0, 1) and spin
+// 2 + hh [6..8] (from mu = 2, 3); after the last hop the last block is exchanged
+// with the partner lane, and the lane owns spins hh and 3 - hh.
+template <int P> constexpr bool split_site() { return P == F64; }
+template <int P> constexpr int threads_per_site() { return split_site<P>() ? 2 : 1; }
+inline int threads_per_site(Prec p) {
+    return p == F64 ? threads_per_site<F64>() : p == DF32 ? threads_per_site<DF32>()
+         : p == F32 ? threads_per_site<F32>() : threads_per_site<F16>();
+}
+// blocks along the sites for a (site_tile x rhs_tile) block: site_tile / threads_per_site sites each
+template <int P> inline int site_blocks(int V, int site_tile) {
+    const int spb = site_tile / threads_per_site<P>();
+    return (V + spb - 1) / spb;
+}
+
+// sign flips as bit operations (no floating-point instruction)
+__device__ __forceinline__ double xsign(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)neg << 63));
+}
+__device__ __forceinline__ float xsign(float x, bool neg) { return __uint_as_float(__float_as_uint(x) ^ ((unsigned)neg << 31)); }
+__device__ __forceinline__ df xsign(df x, bool neg) { return df(xsign(x.hi, neg), xsign(x.lo, neg)); }
+template <class R> __device__ __forceinline__ C<R> cxsign(C<R> a, bool neg) { return C<R>{xsign(a.re, neg), xsign(a.im, neg)}; }
+// f d with f = +-1 (IM = false) or +-i (IM = true), the sign given by neg
+template <bool IM, class R> __device__ __forceinline__ C<R> times_unit(C<R> d, bool neg) {
+    return IM ? C<R>{xsign(d.im, !neg), xsign(d.re, neg)} : cxsign(d, neg);
+}
+
+// the 3 colour components of spin sp of site s (F64 and DF32 layouts: one array per component)
+template <int P, bool NC, class R>
+__device__ __forceinline__ void load_spin(const void *base, int Vs, int s, int sp, C<R> (&v)[3]) {
+    static_assert(P == F64 || P == DF32, "per-component spinor arrays");
+    if constexpr (P == F64) {
+        const double2 *q = reinterpret_cast<const double2 *>(base) + (size_t)(3 * sp) * Vs + s;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 t = ldx<NC>(q + (size_t)c * Vs);
+            v[c] = C<R>{t.x, t.y};
+        }
+    } else {
+        const float4 *q = reinterpret_cast<const float4 *>(base) + (size_t)(3 * sp) * Vs + s;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 t = ldx<NC>(q + (size_t)c * Vs);
+            v[c] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+        }
+    }
+}
+
+// w = U h (ADJ = false) or U^dag h (ADJ = true) for one colour vector
+template <bool ADJ, class R>
+__device__ __forceinline__ void su3_mult1(const C<R> (&u)[9], const C<R> (&h)[3], C<R> (&w)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        C<R> s;
+        if (!ADJ) {
+            s = cmul(u[3 * a + 0], h[0]);
+            s = cmac(s, u[3 * a + 1], h[1]);
+            s = cmac(s, u[3 * a + 2], h[2]);
+        } else {
+            s = cmulc(u[0 + a], h[0]);
+            s = cmacc(s, u[3 + a], h[1]);
+            s = cmacc(s, u[6 + a], h[2]);
+        }
+        w[a] = s;
+    }
+}
+
+// one hop of lane half hh: neighbour site sn, link at index sl of gdir (the adjoint
+// for ADJ), projector sign S, boundary sign flip
+template <int P, int RECON, bool ADJ, int MU, int S, bool NC, class R>
+__device__ __forceinline__ void half_hop(const void *in, int Vs, int sn, const char *gdir, int sl, bool flip, int hh,
+                                         C<R> (&acc)[9]) {
+    constexpr bool IM = MU == 0 || MU == 2;
+    const bool neg = MU == 1 ? hh == 0 : MU == 2 ? hh != 0 : false;
+    const int ps = MU < 2 ? 3 - hh : 2 + hh;
+    C<R> ph[3], pd[3], h[3], u[9], w[3];
+    load_spin<P, NC>(in, Vs, sn, hh, ph);
+    load_spin<P, NC>(in, Vs, sn, ps, pd);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<R> fd = times_unit<IM>(pd[c], neg);
+        h[c] = S > 0 ? cadd(ph[c], fd) : csub(ph[c], fd);
+    }
+    LinkIO<P, RECON>::load(gdir, Vs, sl, u);
+    su3_mult1<ADJ>(u, h, w);
+    constexpr int LO = MU < 2 ? 3 : 6;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<R> wc = cxsign(w[c], flip);
+        acc[c] = cadd(acc[c], wc);
+        const C<R> gw = times_unit<IM>(wc, IM ? !neg : neg);  // conj(f) w
+        acc[LO + c] = S > 0 ? cadd(acc[LO + c], gw) : csub(acc[LO + c], gw);
+    }
+}
+
+template <int P, int RECON, bool DAG, int MU, bool NC, class R>
+__device__ __forceinline__ void half_dir(const Geom &g, const void *in, const char *gdir, int s, int c, int hh,
+                                         C<R> (&acc)[9]) {
+    constexpr int SF = DAG ? +1 : -1;
+    const int L = g.L[MU], st = g.stride[MU];
+    const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+    const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+    half_hop<P, RECON, false, MU, SF, NC>(in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1, hh, acc);
+    half_hop<P, RECON, true, MU, -SF, NC>(in, g.Vs, sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+}
+
+template <int P, int RECON, bool DAG, int MU, bool NC, class R>
+__device__ __forceinline__ void half_dir_eo(const Geom &g, const void *in, const char *gp, const char *gq, int k,
+                                            int n, int c, int hh, C<R> (&acc)[9]) {
+    constexpr int SF = DAG ? +1 : -1;
+    const int L = g.L[MU], st = g.stride[MU];
+    const int nf = (c == L - 1) ? n - (L - 1) * st : n + st;
+    const int nb = (c == 0) ? n + (L - 1) * st : n - st;
+    half_hop<P, RECON, false, MU, SF, NC>(in, g.Vs, nf >> 1, gp, k, MU == 3 && g.antiperiodic && c == L - 1, hh, acc);
+    half_hop<P, RECON, true, MU, -SF, NC>(in, g.Vs, nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+}
+
+// the hopping sum of lane half hh at site s (full lattice) or checkerboard index s (EO)
+template <int P, int RECON, bool DAG, bool EO, bool NC = true>
+__device__ __forceinline__ void hopping_half(const Geom &g, const void *in, const void *gauge, size_t gdir_bytes, int s,
+                                             int hh, C<typename Real<P>::T> (&acc)[9]) {
+    using R = typename Real<P>::T;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = C<R>{R(0), R(0)};
+    if constexpr (EO) {
+        int x, y, z, t;
+        const int n = eo_full_index(g, s, x, y, z, t);
+        const char *gp = reinterpret_cast<const char *>(gauge) + (size_t)(4 * g.eo_parity) * gdir_bytes;
+        const char *gq = reinterpret_cast<const char *>(gauge) + (size_t)(4 * (1 - g.eo_parity)) * gdir_bytes;
+        half_dir_eo<P, RECON, DAG, 0, NC>(g, in, gp, gq, s, n, x, hh, acc);
+        half_dir_eo<P, RECON, DAG, 1, NC>(g, in, gp + gdir_bytes, gq + gdir_bytes, s, n, y, hh, acc);
+        half_dir_eo<P, RECON, DAG, 2, NC>(g, in, gp + 2 * gdir_bytes, gq + 2 * gdir_bytes, s, n, z, hh, acc);
+        half_dir_eo<P, RECON, DAG, 3, NC>(g, in, gp + 3 * gdir_bytes, gq + 3 * gdir_bytes, s, n, t, hh, acc);
+    } else {
+        int rem = s;
+        const int x = rem % g.L[0]; rem /= g.L[0];
+        const int y = rem % g.L[1]; rem /= g.L[1];
+        const int z = rem % g.L[2];
+        const int t = rem / g.L[2];
+        const char *gb = reinterpret_cast<const char *>(gauge);
+        half_dir<P, RECON, DAG, 0, NC>(g, in, gb, s, x, hh, acc);
+        half_dir<P, RECON, DAG, 1, NC>(g, in, gb + gdir_bytes, s, y, hh, acc);
+        half_dir<P, RECON, DAG, 2, NC>(g, in, gb + 2 * gdir_bytes, s, z, hh, acc);
+        half_dir<P, RECON, DAG, 3, NC>(g, in, gb + 3 * gdir_bytes, s, t, hh, acc);
+    }
+}
+
+__device__ __forceinline__ double shfl16(double v) { return __shfl_xor_sync(0xffffffffu, v, 16); }
+__device__ __forceinline__ df shfl16(df v) {
+    return df(__shfl_xor_sync(0xffffffffu, v.hi, 16), __shfl_xor_sync(0xffffffffu, v.lo, 16));
+}
+// spin 2 + hh of this lane's accumulator completes the partner's spin 3 - hh';
+// called by all 32 lanes of the warp
+template <class R> __device__ __forceinline__ void exchange_halves(C<R> (&acc)[9]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<R> o{shfl16(acc[6 + c].re), shfl16(acc[6 + c].im)};
+        acc[3 + c] = cadd(acc[3 + c], o);
+    }
+}
+
+// The components of a site one thread owns in an epilogue: all 12, or the 6 of
+// spins hh and 3 - hh (two lanes per site).  comp(k) is the global component of
+// local component k.
+struct SiteAll {
+    static constexpr int N = 12;
+    __device__ __forceinline__ int comp(int k) const { return k; }
+};
+struct SiteHalf {
+    static constexpr int N = 6;
+    int hh;
+    __device__ __forceinline__ int comp(int k) const { return k < 3 ? 3 * hh + k : 3 * (3 - hh) + k - 3; }
+};
+
+template <int P, class Pt, bool NC = true, class R>
+__device__ __forceinline__ void load_part(const Pt &pt, const void *base, int Vs, int s, C<R> (&v)[Pt::N]) {
+    if constexpr (Pt::N == 12) {
+        SpinorIO<P>::template load<NC>(base, Vs, s, v);
+    } else if constexpr (P == F64) {
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k) {
+            const double2 t = ldx<NC>(reinterpret_cast<const double2 *>(base) + (size_t)pt.comp(k) * Vs + s);
+            v[k] = C<R>{t.x, t.y};
+        }
+    } else if constexpr (P == DF32) {
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k) {
+            const float4 t = ldx<NC>(reinterpret_cast<const float4 *>(base) + (size_t)pt.comp(k) * Vs + s);
+            v[k] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+        }
+    } else {
+        static_assert(P == F32, "partial sites: F64, DF32 and F32 layouts");
+        // component c: half c % 2 of float4 array c / 2
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k) {
+            const int c = pt.comp(k);
+            const float2 t = ldx<NC>(reinterpret_cast<const float2 *>(base) + 2 * ((size_t)(c >> 1) * Vs + s) + (c & 1));
+            v[k] = C<R>{t.x, t.y};
+        }
+    }
+}
+
+template <int P, class Pt, class R>
+__device__ __forceinline__ void store_part(const Pt &pt, void *base, int Vs, int s, const C<R> (&v)[Pt::N]) {
+    if constexpr (Pt::N == 12) {
+        SpinorIO<P>::store(base, Vs, s, v);
+    } else if constexpr (P == F64) {
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k)
+            reinterpret_cast<double2 *>(base)[(size_t)pt.comp(k) * Vs + s] = make_double2(v[k].re, v[k].im);
+    } else if constexpr (P == DF32) {
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k)
+            reinterpret_cast<float4 *>(base)[(size_t)pt.comp(k) * Vs + s] =
+                make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+    } else {
+        static_assert(P == F32, "partial sites: F64, DF32 and F32 layouts");
+#pragma unroll
+        for (int k = 0; k < Pt::N; ++k) {
+            const int c = pt.comp(k);
+            reinterpret_cast<float2 *>(base)[2 * ((size_t)(c >> 1) * Vs + s) + (c & 1)] = make_float2(v[k].re, v[k].im);
+        }
+    }
+}
+
 // Register budget: the FP32 and FP16 kernels are memory-bound and want many
 // resident warps, so they are held to 3 blocks of 256 threads per SM (at most 85
 // registers); FP64 and DF32 are arithmetic-bound and keep the compiler's choice.
@@ -402,18 +637,44 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
     // the field the xpay epilogues add: the hopping input unless another is given
     const void *xin = a.xsrc ? rhs_ptr<R>(a.xsrc, a.xsrc_stride, rr) : in;
     typename Ep::State st{};
-    for (int s0 = blockIdx.x * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
-        const int s = s0 + threadIdx.x;
-        if (row && s < a.g.V) {
-            C<R> acc[12];
-            if constexpr (EO) {
-                if constexpr (P == DF32) hopping_rolled_dir_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                else hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-            } else {
-                if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+    if constexpr (split_site<P>()) {
+        // two lanes per site (blockDim.x a multiple of 32): lane l of warp w of the
+        // block takes site 16 w + (l mod 16), half l / 16
+        const int hh = (threadIdx.x >> 4) & 1;
+        const int sl = ((threadIdx.x >> 5) << 4) | (threadIdx.x & 15);
+        const int spb = blockDim.x >> 1;
+        const SiteHalf pt{hh};
+        for (int s0 = blockIdx.x * spb; s0 < a.g.V; s0 += gridDim.x * spb) {
+            const int s = s0 + sl;
+            const bool on = row && s < a.g.V;
+            C<R> acc[9];
+            if (on) hopping_half<P, RECON, DAG, EO>(a.g, in, a.gauge, a.gauge_dir, s, hh, acc);
+            else
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] = C<R>{R(0), R(0)};
+            exchange_halves(acc);  // warp-uniform: row and s0 are the same for all 32 lanes
+            if (on) {
+                C<R> own[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) own[k] = acc[k];
+                Ep::template site<P>(a, s, r, xin, own, st, pt);
             }
-            Ep::template site<P>(a, s, r, xin, acc, st);
+        }
+    } else {
+        const SiteAll pt{};
+        for (int s0 = blockIdx.x * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
+            const int s = s0 + threadIdx.x;
+            if (row && s < a.g.V) {
+                C<R> acc[12];
+                if constexpr (EO) {
+                    if constexpr (P == DF32) hopping_rolled_dir_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                    else hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                } else {
+                    if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                    else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                }
+                Ep::template site<P>(a, s, r, xin, acc, st, pt);
+            }
         }
     }
     Ep::template finish<P>(a, r, row, st);
@@ -423,15 +684,15 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
 // out = in - kappa * hop     (D or D^dag applied to in)
 struct EpXpay {
     struct State {};
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[12],
-                                                State &) {
-        C<R> p[12];
-        SpinorIO<P>::load(in, a.g.Vs, s, p);
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &, const Pt &pt) {
+        C<R> p[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, p);
         const R k = R(a.kappa);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
-        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
+        for (int c = 0; c < Pt::N; ++c) p[c] = C<R>{p[c].re - k * acc[c].re, p[c].im - k * acc[c].im};
+        store_part<P>(pt, rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, p);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &, int, bool, State &) {}
@@ -440,13 +701,13 @@ struct EpXpay {
 // out = -kappa * hop (no added field); kappa = -1 gives the bare hopping term
 struct EpHop {
     struct State {};
-    template <int P, class R>
-    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *, C<R> (&acc)[12],
-                                                State &) {
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *, C<R> (&acc)[Pt::N],
+                                                State &, const Pt &pt) {
         const R k = R(-a.kappa);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = C<R>{k * acc[c].re, k * acc[c].im};
-        SpinorIO<P>::store(rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, acc);
+        for (int c = 0; c < Pt::N; ++c) acc[c] = C<R>{k * acc[c].re, k * acc[c].im};
+        store_part<P>(pt, rhs_ptr<R>(a.out, a.out_stride, r), a.g.Vs, s, acc);
     }
     template <int P>
     static __device__ __forceinline__ void finish(const DslashArgs &, int, bool, State &) {}

@@ -1,5 +1,5 @@
 // Plain Dslash launches: out = D in or out = D^dag in, every precision and link
-// compression (section 2.1, Eq. (1); section 2.2, gamma5-hermiticity).
+// compression (18, 12 or 8 reals) (section 2.1, Eq. (1); section 2.2, gamma5-hermiticity).
 #include "dslash.cuh"
 #include "wd_host.h"
 
@@ -8,15 +8,17 @@ namespace wd {
 template <int P, int RECON, bool DAG>
 static cudaError_t go(const DslashArgs &a, DslashTiles t, cudaStream_t st) {
     dim3 block(t.site_tile, t.rhs_tile);
-    dim3 grid((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    dim3 grid(site_blocks<P>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
     dslash_kernel<P, RECON, DAG, EpXpay><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int P>
 static cudaError_t go_p(const DslashArgs &a, int recon, bool dagger, DslashTiles t, cudaStream_t st) {
-    if (recon == 12) return dagger ? go<P, 12, true>(a, t, st) : go<P, 12, false>(a, t, st);
-    return dagger ? go<P, 18, true>(a, t, st) : go<P, 18, false>(a, t, st);
+    return with_recon(recon, [&](auto rc) {
+        constexpr int R = decltype(rc)::value;
+        return dagger ? go<P, R, true>(a, t, st) : go<P, R, false>(a, t, st);
+    });
 }
 
 cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, DslashTiles t, cudaStream_t st) {

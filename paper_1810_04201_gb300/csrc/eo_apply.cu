@@ -12,7 +12,7 @@ using namespace wd;
 template <int RECON, bool DAG>
 static cudaError_t schur(const DslashArgs &hop, const DslashArgs &back, DslashTiles t, cudaStream_t st) {
     dim3 block(t.site_tile, 1);
-    dim3 grid((hop.g.V + t.site_tile - 1) / t.site_tile, 1);
+    dim3 grid(site_blocks<F64>(hop.g.V, t.site_tile), 1);
     dslash_kernel<F64, RECON, DAG, EpHop, true><<<grid, block, 0, st>>>(hop);
     dslash_kernel<F64, RECON, DAG, EpXpay, true><<<grid, block, 0, st>>>(back);
     return cudaGetLastError();
@@ -59,9 +59,10 @@ extern "C" wd_status wd_apply_schur(wd_ctx *c, double kappa, const void *in, voi
     b.out = oe;
     b.kappa = kappa * kappa;
     const DslashTiles t = tiles_for(c, F64, 1);
-    cudaError_t err;
-    if (c->recon == 12) err = dagger ? schur<12, true>(h, b, t, c->stream) : schur<12, false>(h, b, t, c->stream);
-    else err = dagger ? schur<18, true>(h, b, t, c->stream) : schur<18, false>(h, b, t, c->stream);
+    const cudaError_t err = with_recon(c->recon, [&](auto rc) {
+        constexpr int R = decltype(rc)::value;
+        return dagger ? schur<R, true>(h, b, t, c->stream) : schur<R, false>(h, b, t, c->stream);
+    });
     WD_CUDA(c, err);
     WD_CUDA(c, cudaMemsetAsync(io, 0, sh, c->stream));
     e.v.a = oe; e.v.a_stride = sh; e.v.c = io; e.v.b = out; e.v.b_stride = sf;

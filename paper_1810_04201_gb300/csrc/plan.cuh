@@ -87,15 +87,21 @@ static int num_sms() {
     return n > 0 ? n : 1;
 }
 
-// Grid for a reducing Dslash: at most the blocks that fit on the machine at once.
-template <class K>
+// Grid for a reducing Dslash (one partial per block and row; the partial buffers hold
+// kMaxPartialBlocks per row).  Up to that many site tiles get one block each and the
+// hardware scheduler balances them across the SMs to the end of the launch; larger
+// lattices get the blocks that are resident at once, each walking many tiles.
+constexpr int kMaxPartialBlocks = 8192;
+template <int P, class K>
 static dim3 reduce_grid(K kernel, const Geom &g, DslashTiles t, int nrhs) {
+    const dim3 rows(1, (nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    const int need = site_blocks<P>(g.V, t.site_tile);
+    if (need <= kMaxPartialBlocks) return dim3(need, rows.y);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, t.site_tile * t.rhs_tile, 0);
     if (per_sm < 1) per_sm = 1;
-    const int need = (g.V + t.site_tile - 1) / t.site_tile;
-    int cap = per_sm * num_sms();
-    return dim3(need < cap ? need : cap, (nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    const int cap = per_sm * num_sms();
+    return dim3(cap < kMaxPartialBlocks ? cap : kMaxPartialBlocks, rows.y);
 }
 
 // Even-odd preconditioning: the solver works on the even half of the lattice
@@ -123,8 +129,8 @@ template <int P, int RECON, bool DAG, class Ep, bool EO = false>
 static void add_dslash(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool reduce) {
     auto k = dslash_kernel<P, RECON, DAG, Ep, EO>;
     dim3 block(t.site_tile, t.rhs_tile);
-    dim3 grid = reduce ? reduce_grid(k, a.g, t, a.nrhs)
-                       : dim3((a.g.V + t.site_tile - 1) / t.site_tile, (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    dim3 grid = reduce ? reduce_grid<P>(k, a.g, t, a.nrhs)
+                       : dim3(site_blocks<P>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
     gb.kernel(k, grid, block, a);
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdio>
 #include <string>
+#include <type_traits>
 #include "wd_internal.cuh"
 
 namespace wd {
@@ -35,6 +36,13 @@ struct EventPair {
         if (e1) cudaEventDestroy(e1);
     }
 };
+
+// Calls f(std::integral_constant<int, R>{}) for the link compression R in {18, 12, 8}.
+template <class F> decltype(auto) with_recon(int recon, F &&f) {
+    if (recon == 12) return f(std::integral_constant<int, 12>{});
+    if (recon == 8) return f(std::integral_constant<int, 8>{});
+    return f(std::integral_constant<int, 18>{});
+}
 
 // workspace: named device buffer of at least `bytes` (kept across calls)
 wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);

@@ -7,6 +7,11 @@
 //   F32 recon-12: 3 arrays of Vs float4
 //   F16 recon-18: 2 arrays of Vs uint4 (8 half2 entries 0-7) + 1 array of Vs half2
 //   F16 recon-12: 1 array of Vs uint4 (entries 0-3) + 1 array of Vs uint2 (entries 4-5)
+//   recon-8 (entries 1, 2, 3 and the phases th0 = arg u[0], th6 = arg u[6]):
+//   F64  4 arrays of Vs double2: u[1], u[2], u[3], (th0, th6)
+//   DF32 4 arrays of Vs float4:  u[1], u[2], u[3], (th0.hi, th0.lo, th6.hi, th6.lo)
+//   F32  2 arrays of Vs float4:  (u[1], u[2]), (u[3], th0, th6)
+//   F16  1 array of Vs uint4:    u[1], u[2], u[3], (th0 / pi, th6 / pi) as half2
 // Link entries have modulus <= 1 (unitary matrices), so FP16 links need no scale.
 #pragma once
 
@@ -26,6 +31,7 @@ enum Prec { F64 = 0, F32 = 1, F16 = 2, DF32 = 3 };
 constexpr int kNumPrec = 4;
 
 constexpr int kSiteAlign = 64;
+constexpr float kPiF = 3.14159265358979f;
 inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
 // ------------------------------------------------------------------ complex
@@ -83,6 +89,7 @@ inline size_t spinor_bytes(Prec p, int Vs) {
     }
 }
 inline size_t link_dir_bytes(Prec p, int recon, int Vs) {
+    if (recon == 8) return (size_t)(p == F64 || p == DF32 ? 4 : p == F32 ? 2 : 1) * Vs * 16;
     if (p == F64 || p == DF32) return (size_t)(recon == 12 ? 6 : 9) * Vs * 16;
     if (p == F32) return recon == 12 ? (size_t)3 * Vs * 16 : (size_t)4 * Vs * 16 + (size_t)Vs * 8;
     return recon == 12 ? (size_t)Vs * 16 + (size_t)Vs * 8 : (size_t)2 * Vs * 16 + (size_t)Vs * 4;
@@ -236,12 +243,62 @@ template <class R> __device__ __forceinline__ void rebuild_row2(C<R> (&u)[9]) {
     u[8] = cconj(csub(cmul(u[0], u[4]), cmul(u[1], u[3])));
 }
 
+// recon-8: the 8-real parametrisation of an SU(3) matrix by its entries u01, u02,
+// u10 and the phases of u00 and u20 (the compression of Clark et al., "Solving
+// lattice QCD systems of equations using mixed precision solvers on GPUs", 2010).
+// With rows a, b, c and n = |a1|^2 + |a2|^2 > 0, unitarity and det U = 1 give
+//   a0 = sqrt(1 - n) e^{i th0},   c0 = sqrt(n - |b0|^2) e^{i th6},
+//   b1 = -(a1 conj(a0) b0 + conj(a2 c0)) / n,   b2 = (conj(a1 c0) - a2 conj(a0) b0) / n,
+//   c1 = (conj(a2 b0) - a1 conj(a0) c0) / n,    c2 = -(conj(a1 b0) + a2 conj(a0) c0) / n,
+// from the two linear conditions that row b (row c) is orthogonal to row a and that
+// c = conj(a x b) (b = conj(c x a)).  CUDA's math library supplies the trig, roots and
+// reciprocal: sincos / sqrt in FP64; in FP32 (the FP32 and FP16 links) the fast
+// __sincosf (absolute error below 2^-21 on [-pi, pi], the range of the stored phases)
+// and __fdividef, whose errors stay within a few FP32 roundings of the link entries.
+// wd_set_gauge rejects gauge fields with n below 1e-6 on some link.
+__device__ __forceinline__ void sincos_lib(double t, double *s, double *c) { sincos(t, s, c); }
+__device__ __forceinline__ void sincos_lib(float t, float *s, float *c) { __sincosf(t, s, c); }
+__device__ __forceinline__ double sqrt_lib(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_lib(float x) { return sqrtf(x); }
+__device__ __forceinline__ double recip_lib(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip_lib(float x) { return __fdividef(1.0f, x); }
+
+template <class R> __device__ __forceinline__ void rebuild_recon8(C<R> (&u)[9], R th0, R th6) {
+    const C<R> a1 = u[1], a2 = u[2], b0 = u[3];
+    const R n = a1.re * a1.re + a1.im * a1.im + a2.re * a2.re + a2.im * a2.im;
+    const R m = n - (b0.re * b0.re + b0.im * b0.im);
+    const R ra = sqrt_lib(R(1) - n > R(0) ? R(1) - n : R(0));
+    const R rc = sqrt_lib(m > R(0) ? m : R(0));
+    R sa, ca, sc, cc;
+    sincos_lib(th0, &sa, &ca);
+    sincos_lib(th6, &sc, &cc);
+    const C<R> a0{ra * ca, ra * sa}, c0{rc * cc, rc * sc};
+    const R inv = recip_lib(n);
+    const C<R> p = cmulc(a0, b0), q = cmulc(a0, c0);  // conj(a0) b0, conj(a0) c0
+    u[0] = a0;
+    u[6] = c0;
+    u[4] = cscale(-inv, cadd(cmul(a1, p), cconj(cmul(a2, c0))));
+    u[5] = cscale(inv, csub(cconj(cmul(a1, c0)), cmul(a2, p)));
+    u[7] = cscale(inv, csub(cconj(cmul(a2, b0)), cmul(a1, q)));
+    u[8] = cscale(-inv, cadd(cconj(cmul(a1, b0)), cmul(a2, q)));
+}
+
 template <int P, int RECON> struct LinkIO;
 
 template <int RECON> struct LinkIO<F64, RECON> {
     using R = double;
     static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
         const double2 *p = reinterpret_cast<const double2 *>(dir_base) + s;
+        if constexpr (RECON == 8) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                double2 t = __ldg(p + (size_t)e * Vs);
+                u[e + 1] = C<R>{t.x, t.y};
+            }
+            const double2 th = __ldg(p + (size_t)3 * Vs);
+            rebuild_recon8(u, th.x, th.y);
+            return;
+        }
         constexpr int n = RECON == 12 ? 6 : 9;
 #pragma unroll
         for (int e = 0; e < n; ++e) {
@@ -256,6 +313,14 @@ template <int RECON> struct LinkIO<F32, RECON> {
     using R = float;
     static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
         const float4 *p = reinterpret_cast<const float4 *>(dir_base) + s;
+        if constexpr (RECON == 8) {
+            const float4 t0 = __ldg(p), t1 = __ldg(p + Vs);
+            u[1] = C<R>{t0.x, t0.y};
+            u[2] = C<R>{t0.z, t0.w};
+            u[3] = C<R>{t1.x, t1.y};
+            rebuild_recon8(u, t1.z, t1.w);
+            return;
+        }
         constexpr int n4 = RECON == 12 ? 3 : 4;
 #pragma unroll
         for (int j = 0; j < n4; ++j) {
@@ -277,6 +342,20 @@ template <int RECON> struct LinkIO<DF32, RECON> {
     using R = df;
     static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
         const float4 *p = reinterpret_cast<const float4 *>(dir_base) + s;
+        if constexpr (RECON == 8) {
+            // the trig and roots need FP64 accuracy: rebuild in double, split back
+            C<double> w[9];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                float4 t = __ldg(p + (size_t)e * Vs);
+                w[e + 1] = C<double>{(double)t.x + (double)t.y, (double)t.z + (double)t.w};
+            }
+            const float4 th = __ldg(p + (size_t)3 * Vs);
+            rebuild_recon8(w, (double)th.x + (double)th.y, (double)th.z + (double)th.w);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) u[e] = C<R>{df(w[e].re), df(w[e].im)};
+            return;
+        }
         constexpr int n = RECON == 12 ? 6 : 9;
 #pragma unroll
         for (int e = 0; e < n; ++e) {
@@ -291,6 +370,15 @@ template <int RECON> struct LinkIO<F16, RECON> {
     using R = float;
     static __device__ __forceinline__ void load(const void *dir_base, int Vs, int s, C<R> (&u)[9]) {
         const uint4 *p = reinterpret_cast<const uint4 *>(dir_base) + s;
+        if constexpr (RECON == 8) {
+            const uint4 t = __ldg(p);
+            const float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), th = h2f(t.w);
+            u[1] = C<R>{a.x, a.y};
+            u[2] = C<R>{b.x, b.y};
+            u[3] = C<R>{c.x, c.y};
+            rebuild_recon8(u, th.x * kPiF, th.y * kPiF);
+            return;
+        }
         if (RECON == 12) {
             uint4 t = __ldg(p);
             float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
@@ -362,17 +450,38 @@ __device__ __forceinline__ bool last_block(unsigned *counter) {
 
 template <int NV>
 __device__ __forceinline__ void sum_partials(const double *partial, int nblk, int nrows, double *tot) {
-    // one warp per (row, k); lanes stride over blocks, then a fixed-order tree
+    // The block has a whole number of warps.  Many sums (rows x NV at least the
+    // warps): one warp per sum, lanes stride over the blocks.  Few sums: every thread
+    // strides over the partials of one sum, combined by a shuffle tree and then warp
+    // by warp in order.  Either way the order is fixed: the same total on every run.
+    __shared__ double wsum[32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-    for (int q = warp; q < nrows * NV; q += nwarp) {
+    if (nrows * NV >= nwarp) {
+        for (int q = warp; q < nrows * NV; q += nwarp) {
+            double s = 0.0;
+            for (int b = lane; b < nblk; b += 32) s += __ldcg(partial + (size_t)q * nblk + b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) tot[q] = s;
+        }
+        __syncthreads();
+        return;
+    }
+    for (int q = 0; q < nrows * NV; ++q) {
         double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += __ldcg(partial + (size_t)q * nblk + b);
+        for (int b = tid; b < nblk; b += nthr) s += __ldcg(partial + (size_t)q * nblk + b);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) tot[q] = s;
+        if (lane == 0) wsum[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarp; ++w) t += wsum[w];
+            tot[q] = t;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // ------------------------------------------------------------------ solver scalars

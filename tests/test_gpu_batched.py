@@ -34,7 +34,7 @@ def make_batch(wd, recon=18):
     return lats, kappas, bs, xs, inputs
 
 
-@pytest.mark.parametrize("inner,recon", [(1, 18), (2, 18), (1, 12)])
+@pytest.mark.parametrize("inner,recon", [(1, 18), (2, 18), (1, 12), (1, 8)])
 def test_batched_matches_oracle(wd, inner, recon):
     lats, kappas, bs, xs, inputs = make_batch(wd, recon)
     res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=inner)

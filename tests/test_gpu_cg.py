@@ -50,7 +50,7 @@ def test_cg_4x4(wd, inner):
 
 
 @pytest.mark.parametrize("inner", [0, 1, 2, 3])
-@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("recon", [18, 12, 8])
 def test_cg_odd_shapes(wd, inner, recon):
     dims, kappa = (6, 6, 6, 8), 0.124
     U = gen.haar_links(dims, seed=3)
@@ -143,7 +143,7 @@ def test_cg_canonical_host_buffers(wd):
     assert st == 0 and oracle.rel_err(xt.numpy(), x_ref) < 1e-9
 
 
-@pytest.mark.parametrize("k,recon,seed", [(12, 18, 7), (5, 12, 8), (1, 18, 9)])
+@pytest.mark.parametrize("k,recon,seed", [(12, 18, 7), (5, 12, 8), (1, 18, 9), (4, 8, 10)])
 def test_block_cg(wd, k, recon, seed):
     """Block CG over k right-hand sides: every column matches the oracle solution."""
     dims, kappa = (4, 4, 4, 8), 0.12
@@ -250,7 +250,7 @@ def test_schur_operator_matches_oracle(wd, dims, dagger):
     assert oracle.rel_err(lat.unpack(out), ref) < 1e-13
 
 
-@pytest.mark.parametrize("inner,recon", [(0, 18), (1, 18), (2, 12), (3, 18)])
+@pytest.mark.parametrize("inner,recon", [(0, 18), (1, 18), (2, 12), (3, 18), (0, 8), (1, 8)])
 def test_even_odd_cg(wd, inner, recon):
     """Even-odd preconditioned CGNR: same solution as the oracle, about half the iterations."""
     dims, kappa = (4, 6, 4, 8), 0.124

@@ -35,7 +35,7 @@ SHAPES = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 6, 6, 8), (3, 5, 4, 6), (8, 8, 8, 12),
 
 @pytest.mark.parametrize("dims", SHAPES)
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
-@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("recon", [18, 12, 8])
 def test_dslash_parity(wd, dims, prec, recon):
     U = gen.haar_links(dims, seed=2)
     psi = gen.gaussian_source(dims, seed=3)
@@ -72,6 +72,11 @@ def test_multi_rhs_parity(wd, nrhs, tiles):
     lat = wd.Lattice(dims)
     lat.set_gauge(U)
     for prec in (0, 1):
+        if prec == 0 and tiles[0] < 32:
+            # FP64 runs two lanes per site: a block needs whole warps along the sites
+            with pytest.raises(wd.WDError):
+                lat.set_tiles(prec, nrhs, *tiles)
+            continue
         lat.set_tiles(prec, nrhs, *tiles)
         f = lat.pack(psi, prec)
         o = lat.new_field(prec, nrhs)
@@ -144,5 +149,48 @@ def test_argument_errors(wd):
         lat.apply(KAPPA, f, lat.new_field(), nrhs=17)
     with pytest.raises(wd.WDError):
         lat.set_tiles(0, 4, 48, 1)
+    with pytest.raises(wd.WDError) as e:
+        lat.set_gauge(gen.unit_links((4, 4, 4, 4)), recon=7)
+    assert e.value.status == 1
     with pytest.raises(wd.WDError):
         wd.Lattice((4, 1, 4, 4))
+
+
+def test_recon8_rejects_singular_links(wd):
+    """The 8-real form divides by |U01|^2 + |U02|^2: unit links are refused, and the
+    context then holds no gauge field until a valid one is set."""
+    dims = (4, 4, 4, 4)
+    lat = wd.Lattice(dims)
+    with pytest.raises(wd.WDError) as e:
+        lat.set_gauge(gen.unit_links(dims), recon=8)
+    assert e.value.status == 1
+    f = lat.pack(gen.gaussian_source(dims, 1))
+    with pytest.raises(wd.WDError) as e:
+        lat.apply(KAPPA, f, lat.new_field())
+    assert e.value.status == 8
+    U = gen.haar_links(dims, seed=6)
+    U[1, 5] = np.eye(3)  # one unit link among Haar links
+    with pytest.raises(wd.WDError):
+        lat.set_gauge(U, recon=8)
+    U = gen.haar_links(dims, seed=6)
+    lat.set_gauge(U, recon=8)
+    psi = gen.gaussian_source(dims, 2)
+    o = lat.new_field()
+    lat.apply(KAPPA, lat.pack(psi), o)
+    assert oracle.rel_err(lat.unpack(o), oracle.apply_D(U, psi, KAPPA, dims)) < TOL[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_recon8_smoothed_links(wd, prec):
+    """Near-unit links (exp(i eps H), the mixed-precision workload) through recon 8."""
+    dims = (6, 4, 4, 8)
+    U = gen.smoothed_links(dims, eps=0.4, seed=12)
+    psi = gen.gaussian_source(dims, seed=13)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=8)
+    f = lat.pack(psi, prec)
+    for dagger in (False, True):
+        o = lat.new_field(prec)
+        lat.apply(KAPPA, f, o, prec, dagger=dagger)
+        ref = oracle.apply_D(U, psi, KAPPA, dims, dagger=dagger)
+        assert oracle.rel_err(lat.unpack(o, prec), ref) < TOL[prec]
