@@ -235,7 +235,7 @@ wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const v
 wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
 /* Fix the tile choice by hand: site_tile in {16, 32, 64, 128, 256} threads,
  * 1 <= rhs_tile <= nrhs, site_tile * rhs_tile <= 256 and a multiple of 32.  WD_F64
- * runs each site on two lanes (site_tile / 2 sites per block) and needs
+ * and WD_DF32 run each site on two lanes (site_tile / 2 sites per block) and need
  * site_tile >= 32.  Unsupported shapes: WD_ERR_ARG. */
 wd_status wd_set_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int site_tile, int rhs_tile);
 

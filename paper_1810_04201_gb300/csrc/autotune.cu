@@ -4,8 +4,8 @@
 //
 // Candidates: site_tile in {16, 32, 64, 128, 256} threads along the sites and
 // rhs_tile in {1, 2, 3, 4, 6, 8, 12, 16} right-hand sides per block, with
-// site_tile * rhs_tile <= 256, a multiple of 32, and rhs_tile <= nrhs (FP64, two
-// lanes per site: site_tile >= 32, i.e. site_tile / 2 sites per block).  Each
+// site_tile * rhs_tile <= 256, a multiple of 32, and rhs_tile <= nrhs (FP64 and
+// DF32, two lanes per site: site_tile >= 32, i.e. site_tile / 2 sites per block).  Each
 // candidate runs the plain D kernel 2 + 5 times on context scratch fields; the
 // fastest mean of the last 5 (CUDA events on the context stream) is kept for
 // (precision, nrhs) and used by every later operator and solver call.
@@ -24,7 +24,7 @@ wd_status wd_set_tiles(wd_ctx *c, wd_prec prec, int nrhs, int site_tile, int rhs
         site_tile * rhs_tile > 256 || (site_tile * rhs_tile) % 32 != 0)
         return fail(c, WD_ERR_ARG, "wd_set_tiles: unsupported tile shape");
     if (threads_per_site((Prec)prec) > 1 && site_tile % 32 != 0)
-        return fail(c, WD_ERR_ARG, "wd_set_tiles: FP64 runs two lanes per site and needs site_tile >= 32");
+        return fail(c, WD_ERR_ARG, "wd_set_tiles: FP64 and DF32 run two lanes per site and need site_tile >= 32");
     DslashTiles t;
     t.site_tile = site_tile;
     t.rhs_tile = rhs_tile;

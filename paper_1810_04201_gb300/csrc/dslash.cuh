@@ -1,8 +1,9 @@
 // Wilson-Dirac hopping term and the Dslash kernel template (sm_103a).
 //
-// One thread computes one output site of one right-hand side.  A thread block is
-// (site_tile x rhs_tile) threads: the rhs_tile right-hand sides of a block read
-// the same links, which the L1 cache then serves once per block.
+// One thread computes one output site of one right-hand side (FP32, FP16), or two
+// lanes of a warp share it (FP64, DF32; see "two lanes per site" below).  A thread
+// block is (site_tile x rhs_tile) threads: the rhs_tile right-hand sides of a block
+// read the same links, which the L1 cache then serves once per block.
 //
 // Per hop (section 2.1, Eq. (1) and Eq. (3); section 2.1, half-spinor remark):
 //   gamma_mu = [[0, A_mu], [A_mu^dag, 0]] in 2x2 spin blocks (Appendix A), with
@@ -216,81 +217,6 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
 // handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
 // one site; Ep::finish runs once per thread after the loop (block and grid
 // reductions, solver scalars).
-// The same hopping sum as a loop over the 4 directions that is not unrolled.  The
-// code of one direction is reused 4 times, so the instruction footprint stays
-// small; used for DF32, whose fully unrolled form (about 9000 instructions per
-// site) is large enough to miss in the instruction cache.
-template <class R>
-__device__ __forceinline__ void project_rt(int mu, int sgn, const C<R> (&p)[12], C<R> (&h)[6]) {
-    if (sgn > 0) {
-        switch (mu) {
-        case 0: project<0, 1>(p, h); break;
-        case 1: project<1, 1>(p, h); break;
-        case 2: project<2, 1>(p, h); break;
-        default: project<3, 1>(p, h); break;
-        }
-    } else {
-        switch (mu) {
-        case 0: project<0, -1>(p, h); break;
-        case 1: project<1, -1>(p, h); break;
-        case 2: project<2, -1>(p, h); break;
-        default: project<3, -1>(p, h); break;
-        }
-    }
-}
-
-template <class R>
-__device__ __forceinline__ void accumulate_rt(int mu, int sgn, C<R> (&acc)[12], const C<R> (&w)[6]) {
-    if (sgn > 0) {
-        switch (mu) {
-        case 0: accumulate<0, 1>(acc, w); break;
-        case 1: accumulate<1, 1>(acc, w); break;
-        case 2: accumulate<2, 1>(acc, w); break;
-        default: accumulate<3, 1>(acc, w); break;
-        }
-    } else {
-        switch (mu) {
-        case 0: accumulate<0, -1>(acc, w); break;
-        case 1: accumulate<1, -1>(acc, w); break;
-        case 2: accumulate<2, -1>(acc, w); break;
-        default: accumulate<3, -1>(acc, w); break;
-        }
-    }
-}
-
-// Each iteration holds the forward and the backward hop of one direction: two
-// independent chains for the scheduler.
-template <int P, int RECON, bool DAG, bool NC = true>
-__device__ __forceinline__ void hopping_rolled_dir(const Geom &g, const void *in, const void *gauge,
-                                                   size_t gdir_bytes, int s, C<typename Real<P>::T> (&acc)[12]) {
-    using R = typename Real<P>::T;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = C<R>{R(0), R(0)};
-    const char *gb = reinterpret_cast<const char *>(gauge);
-    constexpr int SF = DAG ? +1 : -1;
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-        const int L = g.L[mu], st = g.stride[mu];
-        const int cm = (s / st) % L;
-        const int sf = (cm == L - 1) ? s - (L - 1) * st : s + st;
-        const int sb = (cm == 0) ? s + (L - 1) * st : s - st;
-        const bool ff = mu == 3 && g.antiperiodic && cm == L - 1;
-        const bool fb = mu == 3 && g.antiperiodic && cm == 0;
-        const char *gd = gb + (size_t)mu * gdir_bytes;
-        C<R> pf[12], pb[12], hf[6], hb[6], uf[9], ub[9], wf[6], wb[6];
-        SpinorIO<P>::template load<NC>(in, g.Vs, sf, pf);
-        SpinorIO<P>::template load<NC>(in, g.Vs, sb, pb);
-        LinkIO<P, RECON>::load(gd, g.Vs, s, uf);
-        LinkIO<P, RECON>::load(gd, g.Vs, sb, ub);
-        project_rt(mu, SF, pf, hf);
-        project_rt(mu, -SF, pb, hb);
-        su3_mult<false>(uf, hf, wf, ff);
-        su3_mult<true>(ub, hb, wb, fb);
-        accumulate_rt(mu, SF, acc, wf);
-        accumulate_rt(mu, -SF, acc, wb);
-    }
-}
-
 // ---------------------------------------------------------------- checkerboard
 // Even-odd fields hold one parity of the lattice: the site with full index n
 // (parity (x+y+z+t) mod 2) sits at n / 2 of its parity's arrays (all extents
@@ -352,45 +278,13 @@ __device__ __forceinline__ void hopping_eo(const Geom &g, const void *in, const 
     hop_dir_eo<P, RECON, DAG, 3, NC>(g, in, gp + 3 * gdir_bytes, gq + 3 * gdir_bytes, k, n, t, acc);
 }
 
-// checkerboard form of the rolled DF32 loop
-template <int P, int RECON, bool DAG, bool NC = true>
-__device__ __forceinline__ void hopping_rolled_dir_eo(const Geom &g, const void *in, const void *gauge,
-                                                      size_t gdir_bytes, int k, C<typename Real<P>::T> (&acc)[12]) {
-    using R = typename Real<P>::T;
-#pragma unroll
-    for (int q = 0; q < 12; ++q) acc[q] = C<R>{R(0), R(0)};
-    int x, y, z, t;
-    const int n = eo_full_index(g, k, x, y, z, t);
-    const char *gp = reinterpret_cast<const char *>(gauge) + (size_t)(4 * g.eo_parity) * gdir_bytes;
-    const char *gq = reinterpret_cast<const char *>(gauge) + (size_t)(4 * (1 - g.eo_parity)) * gdir_bytes;
-    constexpr int SF = DAG ? +1 : -1;
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-        const int L = g.L[mu], st = g.stride[mu];
-        const int cm = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
-        const int nf = (cm == L - 1) ? n - (L - 1) * st : n + st;
-        const int nb = (cm == 0) ? n + (L - 1) * st : n - st;
-        const bool ff = mu == 3 && g.antiperiodic && cm == L - 1;
-        const bool fb = mu == 3 && g.antiperiodic && cm == 0;
-        C<R> pf[12], pb[12], hf[6], hb[6], uf[9], ub[9], wf[6], wb[6];
-        SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, pf);
-        SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, pb);
-        LinkIO<P, RECON>::load(gp + (size_t)mu * gdir_bytes, g.Vs, k, uf);
-        LinkIO<P, RECON>::load(gq + (size_t)mu * gdir_bytes, g.Vs, nb >> 1, ub);
-        project_rt(mu, SF, pf, hf);
-        project_rt(mu, -SF, pb, hb);
-        su3_mult<false>(uf, hf, wf, ff);
-        su3_mult<true>(ub, hb, wb, fb);
-        accumulate_rt(mu, SF, acc, wf);
-        accumulate_rt(mu, -SF, acc, wb);
-    }
-}
-
 // ---------------------------------------------------------------- two lanes per site
 // FP64 is bound by the FP64 units, which belong to the four schedulers of an SM:
 // a scheduler without warps leaves its unit idle, as in the partial last wave of a
 // launch.  So FP64 sites run on two lanes of a warp, lane l and l ^ 16, and twice
-// as many warps share the work.  Lane half hh computes spin component hh of every
+// as many warps share the work.  DF32 (bound by instruction issue) does the same:
+// half the work per lane needs 128 instead of 255 registers, so twice the warps
+// hide the latencies.  Lane half hh computes spin component hh of every
 // projected half spinor.  Row hh of A_mu has one entry f, in column ps - 2, where
 // ps = 3 - hh for mu = 0, 1 and ps = 2 + hh for mu = 2, 3, so
 //   h_hh = psi_hh + s f psi_ps,   upper spin hh += (U h)_hh,   lower spin ps += s conj(f) (U h)_hh,
@@ -399,7 +293,7 @@ __device__ __forceinline__ void hopping_rolled_dir_eo(const Geom &g, const void 
 // accumulator holds spin hh [0..2], spin 3 - hh [3..5] (from mu = 0, 1) and spin
 // 2 + hh [6..8] (from mu = 2, 3); after the last hop the last block is exchanged
 // with the partner lane, and the lane owns spins hh and 3 - hh.
-template <int P> constexpr bool split_site() { return P == F64; }
+template <int P> constexpr bool split_site() { return P == F64 || P == DF32; }
 template <int P> constexpr int threads_per_site() { return split_site<P>() ? 2 : 1; }
 inline int threads_per_site(Prec p) {
     return p == F64 ? threads_per_site<F64>() : p == DF32 ? threads_per_site<DF32>()
@@ -418,9 +312,10 @@ __device__ __forceinline__ double xsign(double x, bool neg) {
 __device__ __forceinline__ float xsign(float x, bool neg) { return __uint_as_float(__float_as_uint(x) ^ ((unsigned)neg << 31)); }
 __device__ __forceinline__ df xsign(df x, bool neg) { return df(xsign(x.hi, neg), xsign(x.lo, neg)); }
 template <class R> __device__ __forceinline__ C<R> cxsign(C<R> a, bool neg) { return C<R>{xsign(a.re, neg), xsign(a.im, neg)}; }
-// f d with f = +-1 (IM = false) or +-i (IM = true), the sign given by neg
-template <bool IM, class R> __device__ __forceinline__ C<R> times_unit(C<R> d, bool neg) {
-    return IM ? C<R>{xsign(d.im, !neg), xsign(d.re, neg)} : cxsign(d, neg);
+// f d with f = +-1 (im = false) or +-i (im = true), the sign given by neg
+template <class R> __device__ __forceinline__ C<R> times_f(C<R> d, bool im, bool neg) {
+    const C<R> t = im ? C<R>{xsign(d.im, true), d.re} : d;
+    return cxsign(t, neg);
 }
 
 // the 3 colour components of spin sp of site s (F64 and DF32 layouts: one array per component)
@@ -463,54 +358,102 @@ __device__ __forceinline__ void su3_mult1(const C<R> (&u)[9], const C<R> (&h)[3]
     }
 }
 
-// one hop of lane half hh: neighbour site sn, link at index sl of gdir (the adjoint
-// for ADJ), projector sign S, boundary sign flip
-template <int P, int RECON, bool ADJ, int MU, int S, bool NC, class R>
-__device__ __forceinline__ void half_hop(const void *in, int Vs, int sn, const char *gdir, int sl, bool flip, int hh,
-                                         C<R> (&acc)[9]) {
-    constexpr bool IM = MU == 0 || MU == 2;
-    const bool neg = MU == 1 ? hh == 0 : MU == 2 ? hh != 0 : false;
-    const int ps = MU < 2 ? 3 - hh : 2 + hh;
-    C<R> ph[3], pd[3], h[3], u[9], w[3];
-    load_spin<P, NC>(in, Vs, sn, hh, ph);
-    load_spin<P, NC>(in, Vs, sn, ps, pd);
+// Both hops of direction mu for lane half hh.  The forward and backward products
+// enter the upper spin as a sum and the lower spin ps as a difference (the two
+// projectors differ in the sign of s), so the backward product is accumulated onto
+// the forward one (w_f + w_b as one chain of multiply-adds) and the difference
+// is formed as 2 w_f - (w_f + w_b): 6 fewer FP64 operations per lane and direction
+// than two separate hops.  Neighbours: forward spinor index nf with link gf[kf],
+// backward spinor index nb with link gb[kb]; flip_f / flip_b are the boundary signs.
+// mu is a run-time value (constant-folded where the caller unrolls the directions);
+// LO = 3 for mu = 0, 1 and 6 for mu = 2, 3 selects the accumulator block of spin ps.
+
+template <int P, int RECON, bool DAG, int LO, bool NC, class R>
+__device__ __forceinline__ void half_pair(int mu, const void *in, int Vs, int nf, const char *gf, int kf, bool flip_f,
+                                          int nb, const char *gb, int kb, bool flip_b, int hh, C<R> (&acc)[9]) {
+    constexpr int SF = DAG ? +1 : -1;
+    const bool IM = mu == 0 || mu == 2;
+    const bool neg = mu == 1 ? hh == 0 : mu == 2 ? hh != 0 : false;
+    const int ps = mu < 2 ? 3 - hh : 2 + hh;
+    C<R> wf[3], sum[3];
+    {
+        C<R> ph[3], pd[3], h[3], u[9];
+        load_spin<P, NC>(in, Vs, nf, hh, ph);
+        load_spin<P, NC>(in, Vs, nf, ps, pd);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const C<R> fd = times_unit<IM>(pd[c], neg);
-        h[c] = S > 0 ? cadd(ph[c], fd) : csub(ph[c], fd);
+        for (int c = 0; c < 3; ++c) {
+            const C<R> fd = times_f(pd[c], IM, neg);
+            h[c] = cxsign(SF > 0 ? cadd(ph[c], fd) : csub(ph[c], fd), flip_f);
+        }
+        LinkIO<P, RECON>::load(gf, Vs, kf, u);
+        su3_mult1<false>(u, h, wf);
     }
-    LinkIO<P, RECON>::load(gdir, Vs, sl, u);
-    su3_mult1<ADJ>(u, h, w);
-    constexpr int LO = MU < 2 ? 3 : 6;
+    {
+        C<R> ph[3], pd[3], h[3], u[9];
+        load_spin<P, NC>(in, Vs, nb, hh, ph);
+        load_spin<P, NC>(in, Vs, nb, ps, pd);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C<R> fd = times_f(pd[c], IM, neg);
+            h[c] = cxsign(SF > 0 ? csub(ph[c], fd) : cadd(ph[c], fd), flip_b);
+        }
+        LinkIO<P, RECON>::load(gb, Vs, kb, u);
+        // sum = w_f + U^dag h
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C<R> t = cmacc(wf[a], u[0 + a], h[0]);
+            t = cmacc(t, u[3 + a], h[1]);
+            sum[a] = cmacc(t, u[6 + a], h[2]);
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const C<R> wc = cxsign(w[c], flip);
-        acc[c] = cadd(acc[c], wc);
-        const C<R> gw = times_unit<IM>(wc, IM ? !neg : neg);  // conj(f) w
-        acc[LO + c] = S > 0 ? cadd(acc[LO + c], gw) : csub(acc[LO + c], gw);
+        acc[c] = cadd(acc[c], sum[c]);
+        const C<R> d{madd(R(2), wf[c].re, -sum[c].re), madd(R(2), wf[c].im, -sum[c].im)};  // w_f - w_b
+        const C<R> gw = times_f(d, IM, IM ? !neg : neg);                      // conj(f) (w_f - w_b)
+        acc[LO + c] = SF > 0 ? cadd(acc[LO + c], gw) : csub(acc[LO + c], gw);
     }
 }
 
 template <int P, int RECON, bool DAG, int MU, bool NC, class R>
 __device__ __forceinline__ void half_dir(const Geom &g, const void *in, const char *gdir, int s, int c, int hh,
                                          C<R> (&acc)[9]) {
-    constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
     const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
     const int sb = (c == 0) ? s + (L - 1) * st : s - st;
-    half_hop<P, RECON, false, MU, SF, NC>(in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1, hh, acc);
-    half_hop<P, RECON, true, MU, -SF, NC>(in, g.Vs, sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+    half_pair<P, RECON, DAG, MU < 2 ? 3 : 6, NC>(MU, in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1,
+                                                sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc);
 }
 
 template <int P, int RECON, bool DAG, int MU, bool NC, class R>
 __device__ __forceinline__ void half_dir_eo(const Geom &g, const void *in, const char *gp, const char *gq, int k,
                                             int n, int c, int hh, C<R> (&acc)[9]) {
-    constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
     const int nf = (c == L - 1) ? n - (L - 1) * st : n + st;
     const int nb = (c == 0) ? n + (L - 1) * st : n - st;
-    half_hop<P, RECON, false, MU, SF, NC>(in, g.Vs, nf >> 1, gp, k, MU == 3 && g.antiperiodic && c == L - 1, hh, acc);
-    half_hop<P, RECON, true, MU, -SF, NC>(in, g.Vs, nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+    half_pair<P, RECON, DAG, MU < 2 ? 3 : 6, NC>(MU, in, g.Vs, nf >> 1, gp, k, MU == 3 && g.antiperiodic && c == L - 1,
+                                                nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+}
+
+// Directions mu0 and mu0 + 1 as a loop that is not unrolled (DF32: the unrolled
+// code of all directions would miss in the instruction cache).
+template <int P, int RECON, bool DAG, bool EO, int LO, bool NC, class R>
+__device__ __forceinline__ void half_rolled(const Geom &g, const void *in, const char *gp, const char *gq,
+                                            size_t gdir_bytes, int s, int n, const int (&xc)[4], int hh,
+                                            C<R> (&acc)[9]) {
+    const int mu0 = LO == 3 ? 0 : 2;
+#pragma unroll 1
+    for (int mu = mu0; mu < mu0 + 2; ++mu) {
+        const int L = g.L[mu], st = g.stride[mu];
+        const int c = mu == 0 ? xc[0] : mu == 1 ? xc[1] : mu == 2 ? xc[2] : xc[3];  // no indexed register array
+        const int m = EO ? n : s;
+        const int nf = (c == L - 1) ? m - (L - 1) * st : m + st;
+        const int nb = (c == 0) ? m + (L - 1) * st : m - st;
+        const bool ff = mu == 3 && g.antiperiodic && c == L - 1, fb = mu == 3 && g.antiperiodic && c == 0;
+        const char *gf = gp + (size_t)mu * gdir_bytes, *gb = gq + (size_t)mu * gdir_bytes;
+        if (EO) half_pair<P, RECON, DAG, LO, NC>(mu, in, g.Vs, nf >> 1, gf, s, ff, nb >> 1, gb, nb >> 1, fb, hh, acc);
+        else half_pair<P, RECON, DAG, LO, NC>(mu, in, g.Vs, nf, gf, s, ff, nb, gb, nb, fb, hh, acc);
+    }
 }
 
 // the hopping sum of lane half hh at site s (full lattice) or checkerboard index s (EO)
@@ -520,6 +463,24 @@ __device__ __forceinline__ void hopping_half(const Geom &g, const void *in, cons
     using R = typename Real<P>::T;
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = C<R>{R(0), R(0)};
+    if constexpr (P == DF32) {
+        int xc[4], n = s;
+        const char *gp = reinterpret_cast<const char *>(gauge), *gq = gp;
+        if constexpr (EO) {
+            n = eo_full_index(g, s, xc[0], xc[1], xc[2], xc[3]);
+            gp += (size_t)(4 * g.eo_parity) * gdir_bytes;
+            gq += (size_t)(4 * (1 - g.eo_parity)) * gdir_bytes;
+        } else {
+            int rem = s;
+            xc[0] = rem % g.L[0]; rem /= g.L[0];
+            xc[1] = rem % g.L[1]; rem /= g.L[1];
+            xc[2] = rem % g.L[2];
+            xc[3] = rem / g.L[2];
+        }
+        half_rolled<P, RECON, DAG, EO, 3, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, acc);
+        half_rolled<P, RECON, DAG, EO, 6, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, acc);
+        return;
+    }
     if constexpr (EO) {
         int x, y, z, t;
         const int n = eo_full_index(g, s, x, y, z, t);
@@ -666,13 +627,8 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
             const int s = s0 + threadIdx.x;
             if (row && s < a.g.V) {
                 C<R> acc[12];
-                if constexpr (EO) {
-                    if constexpr (P == DF32) hopping_rolled_dir_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                    else hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                } else {
-                    if constexpr (P == DF32) hopping_rolled_dir<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                    else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
-                }
+                if constexpr (EO) hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
                 Ep::template site<P>(a, s, r, xin, acc, st, pt);
             }
         }
