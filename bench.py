@@ -202,10 +202,18 @@ def cpu_baseline(w, U, b, budget_s=20.0):
     t = time.perf_counter() - t0
     n_apply = 2 * info["iters"] + 5  # setup 2, per iteration 2, true residual 3
     gflops = n_apply * FLOP_PER_SITE * V / t / 1e9
+    # the same operator on one core, for the per-core rate
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.apply_D(U, b1, w["kappa"], dims)
+    t1 = time.perf_counter() - t0
+    oracle.set_threads(threads)
     return {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"oracle CGNR on the same {'x'.join(map(str, dims))} lattice and source, "
                       f"{info['iters']} iterations ({n_apply} operator applications) in {t:.1f} s, "
-                      f"{threads} OpenMP threads; 1320 flop/site per application"}
+                      f"{threads} OpenMP threads; 1320 flop/site per application",
+            "dslash_gflops_all_cores": round(FLOP_PER_SITE * V / t_apply / 1e9, 4),
+            "dslash_gflops_one_core": round(FLOP_PER_SITE * V / t1 / 1e9, 4)}
 
 
 def run_reference(args, w, rank, world):

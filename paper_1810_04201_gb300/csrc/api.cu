@@ -195,6 +195,7 @@ wd_status wd_set_stream(wd_ctx *c, void *stream) {
 }
 
 wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
+    wd::NvtxRange nvtx_("wd_set_gauge");
     if (!c) return WD_ERR_ARG;
     if (!U) return fail(c, WD_ERR_ARG, "wd_set_gauge: null gauge pointer");
     if (recon != 18 && recon != 12 && recon != 8) return fail(c, WD_ERR_ARG, "wd_set_gauge: recon must be 18, 12 or 8");
@@ -266,6 +267,7 @@ static wd_status canon_stage(wd_ctx *c, const double *canon, int nrhs, int on_de
 }
 
 wd_status wd_pack(wd_ctx *c, const double *canon, int on_device, void *field, wd_prec prec, int nrhs) {
+    wd::NvtxRange nvtx_("wd_pack");
     if (!c) return WD_ERR_ARG;
     if (!canon || !field || bad_prec(prec) || nrhs < 1 || nrhs > WD_MAX_RHS)
         return fail(c, WD_ERR_ARG, "wd_pack: bad argument");
@@ -288,6 +290,7 @@ wd_status wd_pack(wd_ctx *c, const double *canon, int on_device, void *field, wd
 }
 
 wd_status wd_unpack(wd_ctx *c, const void *field, wd_prec prec, int nrhs, double *canon, int on_device) {
+    wd::NvtxRange nvtx_("wd_unpack");
     if (!c) return WD_ERR_ARG;
     if (!canon || !field || bad_prec(prec) || nrhs < 1 || nrhs > WD_MAX_RHS)
         return fail(c, WD_ERR_ARG, "wd_unpack: bad argument");
@@ -340,16 +343,19 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
 }
 
 wd_status wd_apply(wd_ctx *c, double kappa, const void *in, void *out, wd_prec prec, int nrhs) {
+    wd::NvtxRange nvtx_("wd_apply");
     if (c) c->launches = 0;
     return apply_common(c, kappa, in, out, prec, nrhs, false, "wd_apply");
 }
 
 wd_status wd_apply_dagger(wd_ctx *c, double kappa, const void *in, void *out, wd_prec prec, int nrhs) {
+    wd::NvtxRange nvtx_("wd_apply_dagger");
     if (c) c->launches = 0;
     return apply_common(c, kappa, in, out, prec, nrhs, true, "wd_apply_dagger");
 }
 
 wd_status wd_normal_apply(wd_ctx *c, double kappa, const void *in, void *out, wd_prec prec, int nrhs) {
+    wd::NvtxRange nvtx_("wd_normal_apply");
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (bad_prec(prec) || nrhs < 1 || nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_normal_apply: bad argument");

@@ -33,6 +33,7 @@ wd_status wd_set_tiles(wd_ctx *c, wd_prec prec, int nrhs, int site_tile, int rhs
 }
 
 wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile) {
+    wd::NvtxRange nvtx_("wd_autotune");
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if ((int)prec < 0 || (int)prec >= kNumPrec || nrhs < 1 || nrhs > WD_MAX_RHS)

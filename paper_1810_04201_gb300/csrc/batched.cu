@@ -431,6 +431,7 @@ static cudaError_t build_batched(BatchArgs &a, cudaGraphExec_t *exec) {
 
 extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const void *const *b,
                                          void *const *x, int n, const wd_cg_params *prm, wd_cg_result *res) {
+    wd::NvtxRange nvtx_("wd_cg_solve_batched");
     if (!ctxs || n < 1 || !ctxs[0]) return WD_ERR_ARG;
     wd_ctx *c0 = ctxs[0];
     c0->launches = 0;

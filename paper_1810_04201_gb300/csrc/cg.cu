@@ -61,6 +61,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
 extern "C" {
 
 wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm, wd_cg_result *res) {
+    wd::NvtxRange nvtx_("wd_cg_solve");
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (!b || !x || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve: null argument");
@@ -246,6 +247,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
 
 wd_status wd_cg_solve_canonical(wd_ctx *c, double kappa, const double *b_canon, double *x_canon, int on_device,
                                 const wd_cg_params *prm, wd_cg_result *res) {
+    wd::NvtxRange nvtx_("wd_cg_solve_canonical");
     if (!c) return WD_ERR_ARG;
     if (!b_canon || !x_canon || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve_canonical: null argument");
     const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;

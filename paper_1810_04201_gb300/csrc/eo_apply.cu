@@ -19,6 +19,7 @@ static cudaError_t schur(const DslashArgs &hop, const DslashArgs &back, DslashTi
 }
 
 extern "C" wd_status wd_apply_schur(wd_ctx *c, double kappa, const void *in, void *out, int dagger) {
+    wd::NvtxRange nvtx_("wd_apply_schur");
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (!in || !out || in == out) return fail(c, WD_ERR_ARG, "wd_apply_schur: bad field pointers");

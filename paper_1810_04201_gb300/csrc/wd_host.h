@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <string>
 #include <type_traits>
+#include <nvtx3/nvToolsExt.h>
 #include "wd_internal.cuh"
 
 namespace wd {
@@ -18,6 +19,15 @@ wd_status cuda_fail(wd_ctx *c, cudaError_t e, const char *where);
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return ::wd::cuda_fail(ctx, e_, #call); \
     } while (0)
+
+// An NVTX range over one library call (seen by profilers that record NVTX, e.g.
+// ncu --nvtx --nvtx-include "wd_cg_solve/"); free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // A pair of CUDA events released on every return path.
 struct EventPair {

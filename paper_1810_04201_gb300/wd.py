@@ -3,12 +3,13 @@
 Every step of the computation runs in the library's CUDA kernels; this module
 converts Python arguments into C arguments, uses torch for device memory and
 for the current CUDA stream, and turns status codes into exceptions.  There is
-no CPU fallback: importing the binding loads ``_build/libwd.so`` and raises if
-it is missing.
+no CPU fallback: creating a Lattice (or calling cg_batched) loads
+``_build/libwd.so`` and raises if it is missing.
 """
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -106,6 +107,7 @@ class Lattice:
         self.dims = tuple(int(d) for d in dims)
         self.V = int(np.prod(self.dims))
         self.ctx = ctypes.c_void_p()
+        self.recon = 18
         d = (ctypes.c_int * 4)(*self.dims)
         st = self.lib.wd_create(ctypes.byref(self.ctx), d, int(bool(antiperiodic_t)), _stream_ptr(stream))
         if st != 0:
@@ -155,6 +157,7 @@ class Lattice:
             assert a.shape == (4, self.V, 3, 3)
             self._check(self.lib.wd_set_gauge(self.ctx, a.ctypes.data_as(ctypes.c_void_p), 0, recon),
                         "wd_set_gauge")
+        self.recon = int(recon)
 
     def pack(self, psi, prec=WD_F64, out=None):
         """Canonical spinor(s) (numpy or cuda complex128, (V,4,3) or (nrhs,V,4,3)) -> field."""
@@ -239,13 +242,68 @@ class Lattice:
             self._check(st, "wd_cg_solve_canonical")
         return [r.as_dict() for r in res], st
 
-    def autotune(self, prec=WD_F64, nrhs=1):
+    def autotune(self, prec=WD_F64, nrhs=1, cache=None):
+        """Time the launch shapes (wd_autotune) and keep the fastest.  With a cache path
+        (or WD_TILE_CACHE set), a shape found before for the same lattice, precision, link
+        compression, nrhs and device is reused without timing, and new results are added."""
+        path = cache or os.environ.get("WD_TILE_CACHE")
+        key = None
+        if path:
+            key = tile_cache_key(self.dims, prec, self.recon, nrhs, device_tag())
+            hit = TileCache(path).get(key)
+            if hit is not None:
+                self.set_tiles(prec, nrhs, *hit)
+                return hit
         st_, rt = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.wd_autotune(self.ctx, prec, nrhs, ctypes.byref(st_), ctypes.byref(rt)), "wd_autotune")
+        if path:
+            TileCache(path).put(key, (st_.value, rt.value))
         return st_.value, rt.value
 
     def set_tiles(self, prec, nrhs, site_tile, rhs_tile):
         self._check(self.lib.wd_set_tiles(self.ctx, prec, nrhs, site_tile, rhs_tile), "wd_set_tiles")
+
+
+def device_tag() -> str:
+    """Name and compute capability of the current CUDA device."""
+    i = torch.cuda.current_device()
+    major, minor = torch.cuda.get_device_capability(i)
+    return f"{torch.cuda.get_device_name(i)}|sm_{major}{minor}"
+
+
+def tile_cache_key(dims, prec, recon, nrhs, device) -> str:
+    return f"{'x'.join(str(int(d)) for d in dims)}|prec{int(prec)}|recon{int(recon)}|nrhs{int(nrhs)}|{device}"
+
+
+class TileCache:
+    """Autotuned launch shapes on disk: a JSON object {key: [site_tile, rhs_tile]}.
+    Writes go to a temporary file that replaces the old one, so a reader never sees a
+    partial file; an unreadable file counts as empty."""
+
+    def __init__(self, path):
+        self.path = os.fspath(path)
+
+    def load(self) -> dict:
+        try:
+            with open(self.path) as f:
+                d = json.load(f)
+            return d if isinstance(d, dict) else {}
+        except (OSError, ValueError):
+            return {}
+
+    def get(self, key):
+        v = self.load().get(key)
+        if isinstance(v, list) and len(v) == 2 and all(isinstance(t, int) for t in v):
+            return int(v[0]), int(v[1])
+        return None
+
+    def put(self, key, tiles) -> None:
+        d = self.load()
+        d[key] = [int(tiles[0]), int(tiles[1])]
+        tmp = f"{self.path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
 
 
 def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32, delta=0.0):

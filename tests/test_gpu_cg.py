@@ -308,3 +308,44 @@ def test_canonical_pageable_host_buffers(wd):
     res, st = lat.cg_canonical(kappa, b, x, tol=1e-10, precondition=1)
     x_ref, _ = ref_solution(U, b, kappa, dims)
     assert st == 0 and oracle.rel_err(x, x_ref) < 1e-9
+
+
+def test_corrupted_inputs_give_statuses_not_hangs(wd):
+    """A NaN link or an infinite source entry ends the solve with WD_ERR_NONFINITE in
+    every inner precision (and in the batched solver), never with a hang."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=1)
+    b = gen.gaussian_source(dims, seed=2)
+    Ubad = U.copy()
+    Ubad[2, 17, 1, 0] = np.nan
+    lat = wd.Lattice(dims)
+    lat.set_gauge(Ubad)
+    for inner in (0, 1, 2, 3):
+        res, st = lat.cg(kappa, lat.pack(b), lat.new_field(), tol=1e-10, inner=inner, raise_on_fail=False)
+        assert st == 6 and res[0]["status"] == 6, inner
+    lat.set_gauge(U)
+    binf = b.copy()
+    binf[3, 0, 0] = np.inf
+    res, st = lat.cg(kappa, lat.pack(binf), lat.new_field(), tol=1e-10, raise_on_fail=False)
+    assert st == 6
+    res, st = wd.cg_batched([lat], [kappa], [lat.pack(binf)], [lat.new_field()], tol=1e-10)
+    assert res[0]["status"] == 6
+
+
+def test_autotune_cache_file(wd, tmp_path):
+    """Tiles tuned once are stored under (lattice, precision, links, nrhs, device) and
+    reused by a later context without timing."""
+    import json
+    dims = (8, 8, 8, 8)
+    path = tmp_path / "tiles.json"
+    lat = wd.Lattice(dims)
+    lat.set_gauge(gen.haar_links(dims, seed=3), recon=12)
+    t1 = lat.autotune(1, 4, cache=path)
+    key = wd.tile_cache_key(dims, 1, 12, 4, wd.device_tag())
+    assert json.loads(path.read_text())[key] == list(t1)
+    lat2 = wd.Lattice(dims)
+    lat2.set_gauge(gen.haar_links(dims, seed=3), recon=12)
+    before = lat2.launches
+    assert lat2.autotune(1, 4, cache=path) == t1
+    assert lat2.launches == before  # no timing launches
+    assert lat2.autotune(1, 2, cache=path) != () and len(json.loads(path.read_text())) == 2

@@ -117,7 +117,8 @@ def test_pack_unpack_roundtrip_bit_exact(wd):
 
 @pytest.mark.parametrize("dims", [(16, 16, 16, 16), (32, 32, 32, 64)])
 def test_full_size_sampled(wd, dims):
-    """Full-size lattices: GPU output compared with the oracle at sampled sites."""
+    """Full-size lattices: GPU output compared with the oracle at sampled sites, every
+    precision and link compression."""
     U = gen.haar_links(dims, seed=10) if dims[3] == 16 else gen.smoothed_links(dims, seed=6, eps=0.4)
     psi = gen.gaussian_source(dims, seed=11)
     lat = wd.Lattice(dims)
@@ -125,14 +126,16 @@ def test_full_size_sampled(wd, dims):
     V = int(np.prod(dims))
     sites = np.unique(np.concatenate([np.arange(64), V - 1 - np.arange(64),
                                       gen.uniform(3, 9, 0, 256).__mul__(V).astype(np.int64)]))
-    for prec in (0, 1, 3):
-        f = lat.pack(psi, prec)
-        o = lat.new_field(prec)
-        for dagger in (False, True):
-            lat.apply(KAPPA, f, o, prec, dagger=dagger)
-            got = lat.unpack(o, prec)[sites]
-            ref = oracle.apply_D_sites(U, psi, KAPPA, dims, sites, dagger=dagger)
-            assert oracle.rel_err(got, ref) < TOL[prec]
+    for recon in (18, 12, 8):
+        lat.set_gauge(U, recon=recon)
+        for prec in (0, 1, 2, 3):
+            f = lat.pack(psi, prec)
+            o = lat.new_field(prec)
+            for dagger in (False, True):
+                lat.apply(KAPPA, f, o, prec, dagger=dagger)
+                got = lat.unpack(o, prec)[sites]
+                ref = oracle.apply_D_sites(U, psi, KAPPA, dims, sites, dagger=dagger)
+                assert oracle.rel_err(got, ref) < TOL[prec], (recon, prec, dagger)
 
 
 def test_argument_errors(wd):
@@ -194,3 +197,27 @@ def test_recon8_smoothed_links(wd, prec):
         lat.apply(KAPPA, f, o, prec, dagger=dagger)
         ref = oracle.apply_D(U, psi, KAPPA, dims, dagger=dagger)
         assert oracle.rel_err(lat.unpack(o, prec), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("recon", [18, 8])
+def test_outputs_fully_written_over_nan_poison(wd, recon):
+    """Output buffers filled with NaN bytes before each call: every site of every
+    right-hand side is overwritten (no unwritten tail or tile)."""
+    dims, nrhs = (6, 4, 4, 6), 3
+    U = gen.haar_links(dims, seed=21)
+    psi = gen.gaussian_source(dims, seed=22, nrhs=nrhs)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=recon)
+    for prec in (0, 1, 2, 3):
+        f = lat.pack(psi, prec)
+        for call in (lat.apply, lat.normal_apply):
+            o = lat.new_field(prec, nrhs)
+            o.fill_(0xFF)
+            call(KAPPA, f, o, prec, nrhs=nrhs)
+            got = lat.unpack(o, prec, nrhs)
+            assert np.isfinite(got).all(), (prec, call.__name__)
+            for r in range(nrhs):
+                ref = oracle.apply_D(U, psi[r], KAPPA, dims)
+                if call == lat.normal_apply:
+                    ref = oracle.apply_Ddag(U, ref, KAPPA, dims)
+                assert oracle.rel_err(got[r], ref) < 4 * TOL[prec], (prec, call.__name__, r)
