@@ -31,7 +31,7 @@
  *   WD_F32: 6 arrays of Vs float4 (two complex64 components each);
  *   WD_F16: 3 arrays of Vs x 16 B (four half2 components each), then Vs floats
  *           holding the per-site scale (the component of largest magnitude);
- *   WD_DF32: 12 arrays of Vs float4 (re.hi, re.lo, im.hi, im.lo);
+ *   WD_DF32: 12 arrays of Vs float4 (re.hi, im.hi, re.lo, im.lo);
  * where Vs is V rounded up to a multiple of 64.  Right-hand sides follow each
  * other at a stride of wd_field_bytes(ctx, prec, 1).  Fields must be 256-byte
  * aligned (torch and cudaMalloc allocations are).

@@ -144,10 +144,10 @@ __device__ __forceinline__ void pack_link(const double2 *u, char *base, int Vs, 
             float4 *d = reinterpret_cast<float4 *>(base) + idx;
             for (int e = 0; e < 3; ++e) {
                 const df re(u[e + 1].x), im(u[e + 1].y);
-                d[(size_t)e * Vs] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                d[(size_t)e * Vs] = make_float4(re.hi, im.hi, re.lo, im.lo);
             }
             const df t0(th0), t6(th6);
-            d[(size_t)3 * Vs] = make_float4(t0.hi, t0.lo, t6.hi, t6.lo);
+            d[(size_t)3 * Vs] = make_float4(t0.hi, t6.hi, t0.lo, t6.lo);
         } else if (P == F32) {
             float4 *d = reinterpret_cast<float4 *>(base) + idx;
             d[0] = make_float4((float)u[1].x, (float)u[1].y, (float)u[2].x, (float)u[2].y);
@@ -168,7 +168,7 @@ __device__ __forceinline__ void pack_link(const double2 *u, char *base, int Vs, 
         float4 *d = reinterpret_cast<float4 *>(base) + idx;
         for (int e = 0; e < n; ++e) {
             const df re(u[e].x), im(u[e].y);
-            d[(size_t)e * Vs] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            d[(size_t)e * Vs] = make_float4(re.hi, im.hi, re.lo, im.lo);
         }
     } else if (P == F32) {
         float4 *d = reinterpret_cast<float4 *>(base) + idx;

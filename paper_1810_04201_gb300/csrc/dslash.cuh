@@ -334,7 +334,7 @@ __device__ __forceinline__ void load_spin(const void *base, int Vs, int s, int s
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float4 t = ldx<NC>(q + (size_t)c * Vs);
-            v[c] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+            v[c] = C<R>{df(t.x, t.z), df(t.y, t.w)};
         }
     }
 }
@@ -435,12 +435,118 @@ __device__ __forceinline__ void half_dir_eo(const Geom &g, const void *in, const
                                                 nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, hh, acc);
 }
 
+// ------------------------------------------------------------ DF32 on packed pairs
+// The DF32 form of half_pair: every complex df value is a cd2 (high parts and low
+// parts packed), so each add, product and TwoSum step handles the real and the
+// imaginary part in one f32x2 instruction.  Complex products are written as
+// h u = h.re u + h.im (i u) and conj(u) h = h.re conj(u) + h.im (i conj(u)), with the
+// parts of h broadcast once and reused by the three rows of the link.
+template <bool NC>
+__device__ __forceinline__ void load_spin_cd(const void *base, int Vs, int s, int sp, cd2 (&v)[3]) {
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base) + (size_t)(3 * sp) * Vs + s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const ulonglong2 t = ldx<NC>(q + (size_t)c * Vs);
+        v[c] = cd2{t.x, t.y};
+    }
+}
+
+template <int RECON>
+__device__ __forceinline__ void load_link_cd(const char *gdir, int Vs, int s, cd2 (&u)[9]) {
+    if constexpr (RECON == 18) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(gdir) + s;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const ulonglong2 t = __ldg(p + (size_t)e * Vs);
+            u[e] = cd2{t.x, t.y};
+        }
+    } else {
+        C<df> w[9];
+        LinkIO<DF32, RECON>::load(gdir, Vs, s, w);
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            u[e] = cd2{f2_pack(w[e].re.hi, w[e].im.hi), f2_pack(w[e].re.lo, w[e].im.lo)};
+    }
+}
+
+// f z for f = +-1 or +-i
+__device__ __forceinline__ cd2 cd_times_f(cd2 z, bool im, bool neg) { return cd_neg_if(im ? cd_muli(z) : z, neg); }
+
+template <int RECON, bool DAG, int LO, bool NC>
+__device__ __forceinline__ void half_pair_cd(int mu, const void *in, int Vs, int nf, const char *gf, int kf,
+                                             bool flip_f, int nb, const char *gb, int kb, bool flip_b, int hh,
+                                             cd2 (&acc)[9]) {
+    constexpr int SF = DAG ? +1 : -1;
+    const bool IM = mu == 0 || mu == 2;
+    const bool neg = mu == 1 ? hh == 0 : mu == 2 ? hh != 0 : false;
+    const int ps = mu < 2 ? 3 - hh : 2 + hh;
+    cd2 wf[3], sum[3];
+    {
+        cd2 ph[3], pd[3], u[9];
+        bc2 hr[3], hi[3];
+        load_spin_cd<NC>(in, Vs, nf, hh, ph);
+        load_spin_cd<NC>(in, Vs, nf, ps, pd);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cd2 fd = cd_times_f(pd[c], IM, neg);
+            const cd2 h = cd_neg_if(SF > 0 ? cd_add(ph[c], fd) : cd_sub(ph[c], fd), flip_f);
+            hr[c] = bc_re(h);
+            hi[c] = bc_im(h);
+        }
+        load_link_cd<RECON>(gf, Vs, kf, u);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cd2 t = cd_mul(hr[0], u[3 * a]);
+            t = cd_mac(t, hi[0], cd_muli(u[3 * a]));
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                t = cd_mac(t, hr[b], u[3 * a + b]);
+                t = cd_mac(t, hi[b], cd_muli(u[3 * a + b]));
+            }
+            wf[a] = t;
+        }
+    }
+    {
+        cd2 ph[3], pd[3], u[9];
+        bc2 hr[3], hi[3];
+        load_spin_cd<NC>(in, Vs, nb, hh, ph);
+        load_spin_cd<NC>(in, Vs, nb, ps, pd);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cd2 fd = cd_times_f(pd[c], IM, neg);
+            const cd2 h = cd_neg_if(SF > 0 ? cd_sub(ph[c], fd) : cd_add(ph[c], fd), flip_b);
+            hr[c] = bc_re(h);
+            hi[c] = bc_im(h);
+        }
+        load_link_cd<RECON>(gb, Vs, kb, u);
+        // sum = w_f + U^dag h
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cd2 t = wf[a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cd2 cu = cd_conj(u[3 * b + a]);
+                t = cd_mac(t, hr[b], cu);
+                t = cd_mac(t, hi[b], cd_muli(cu));
+            }
+            sum[a] = t;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = cd_add(acc[c], sum[c]);
+        const cd2 d = cd_sub(cd_twice(wf[c]), sum[c]);      // w_f - w_b
+        const cd2 gw = cd_times_f(d, IM, IM ? !neg : neg);  // conj(f) (w_f - w_b)
+        acc[LO + c] = SF > 0 ? cd_add(acc[LO + c], gw) : cd_sub(acc[LO + c], gw);
+    }
+}
+
 // Directions mu0 and mu0 + 1 as a loop that is not unrolled (DF32: the unrolled
 // code of all directions would miss in the instruction cache).
-template <int P, int RECON, bool DAG, bool EO, int LO, bool NC, class R>
+template <int RECON, bool DAG, bool EO, int LO, bool NC>
 __device__ __forceinline__ void half_rolled(const Geom &g, const void *in, const char *gp, const char *gq,
                                             size_t gdir_bytes, int s, int n, const int (&xc)[4], int hh,
-                                            C<R> (&acc)[9]) {
+                                            cd2 (&acc)[9]) {
     const int mu0 = LO == 3 ? 0 : 2;
 #pragma unroll 1
     for (int mu = mu0; mu < mu0 + 2; ++mu) {
@@ -451,8 +557,8 @@ __device__ __forceinline__ void half_rolled(const Geom &g, const void *in, const
         const int nb = (c == 0) ? m + (L - 1) * st : m - st;
         const bool ff = mu == 3 && g.antiperiodic && c == L - 1, fb = mu == 3 && g.antiperiodic && c == 0;
         const char *gf = gp + (size_t)mu * gdir_bytes, *gb = gq + (size_t)mu * gdir_bytes;
-        if (EO) half_pair<P, RECON, DAG, LO, NC>(mu, in, g.Vs, nf >> 1, gf, s, ff, nb >> 1, gb, nb >> 1, fb, hh, acc);
-        else half_pair<P, RECON, DAG, LO, NC>(mu, in, g.Vs, nf, gf, s, ff, nb, gb, nb, fb, hh, acc);
+        if (EO) half_pair_cd<RECON, DAG, LO, NC>(mu, in, g.Vs, nf >> 1, gf, s, ff, nb >> 1, gb, nb >> 1, fb, hh, acc);
+        else half_pair_cd<RECON, DAG, LO, NC>(mu, in, g.Vs, nf, gf, s, ff, nb, gb, nb, fb, hh, acc);
     }
 }
 
@@ -477,8 +583,18 @@ __device__ __forceinline__ void hopping_half(const Geom &g, const void *in, cons
             xc[2] = rem % g.L[2];
             xc[3] = rem / g.L[2];
         }
-        half_rolled<P, RECON, DAG, EO, 3, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, acc);
-        half_rolled<P, RECON, DAG, EO, 6, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, acc);
+        cd2 a9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a9[k] = cd2{0ull, 0ull};
+        half_rolled<RECON, DAG, EO, 3, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, a9);
+        half_rolled<RECON, DAG, EO, 6, NC>(g, in, gp, gq, gdir_bytes, s, n, xc, hh, a9);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float rh, ih, rl, il;
+            f2_unpack(a9[k].hi, rh, ih);
+            f2_unpack(a9[k].lo, rl, il);
+            acc[k] = C<R>{df(rh, rl), df(ih, il)};
+        }
         return;
     }
     if constexpr (EO) {
@@ -545,7 +661,7 @@ __device__ __forceinline__ void load_part(const Pt &pt, const void *base, int Vs
 #pragma unroll
         for (int k = 0; k < Pt::N; ++k) {
             const float4 t = ldx<NC>(reinterpret_cast<const float4 *>(base) + (size_t)pt.comp(k) * Vs + s);
-            v[k] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+            v[k] = C<R>{df(t.x, t.z), df(t.y, t.w)};
         }
     } else {
         static_assert(P == F32, "partial sites: F64, DF32 and F32 layouts");
@@ -571,7 +687,7 @@ __device__ __forceinline__ void store_part(const Pt &pt, void *base, int Vs, int
 #pragma unroll
         for (int k = 0; k < Pt::N; ++k)
             reinterpret_cast<float4 *>(base)[(size_t)pt.comp(k) * Vs + s] =
-                make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+                make_float4(v[k].re.hi, v[k].im.hi, v[k].re.lo, v[k].im.lo);
     } else {
         static_assert(P == F32, "partial sites: F64, DF32 and F32 layouts");
 #pragma unroll

@@ -9,7 +9,7 @@
 //   F16 recon-12: 1 array of Vs uint4 (entries 0-3) + 1 array of Vs uint2 (entries 4-5)
 //   recon-8 (entries 1, 2, 3 and the phases th0 = arg u[0], th6 = arg u[6]):
 //   F64  4 arrays of Vs double2: u[1], u[2], u[3], (th0, th6)
-//   DF32 4 arrays of Vs float4:  u[1], u[2], u[3], (th0.hi, th0.lo, th6.hi, th6.lo)
+//   DF32 4 arrays of Vs float4:  u[1], u[2], u[3], (th0.hi, th6.hi, th0.lo, th6.lo)
 //   F32  2 arrays of Vs float4:  (u[1], u[2]), (u[3], th0, th6)
 //   F16  1 array of Vs uint4:    u[1], u[2], u[3], (th0 / pi, th6 / pi) as half2
 // Link entries have modulus <= 1 (unitary matrices), so FP16 links need no scale.
@@ -149,7 +149,8 @@ template <> struct SpinorIO<F32> {
     }
 };
 
-// DF32: one float4 (re.hi, re.lo, im.hi, im.lo) per complex component, 12 arrays.
+// DF32: one float4 (re.hi, im.hi, re.lo, im.lo) per complex component, 12 arrays: a
+// 128-bit load gives the high parts and the low parts as two aligned float pairs.
 template <> struct SpinorIO<DF32> {
     using R = df;
     template <bool NC = true>
@@ -158,13 +159,13 @@ template <> struct SpinorIO<DF32> {
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             float4 t = ldx<NC>(p + (size_t)c * Vs);
-            v[c] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+            v[c] = C<R>{df(t.x, t.z), df(t.y, t.w)};
         }
     }
     static __device__ __forceinline__ void store(void *base, int Vs, int s, const C<R> (&v)[12]) {
         float4 *p = reinterpret_cast<float4 *>(base) + s;
 #pragma unroll
-        for (int c = 0; c < 12; ++c) p[(size_t)c * Vs] = make_float4(v[c].re.hi, v[c].re.lo, v[c].im.hi, v[c].im.lo);
+        for (int c = 0; c < 12; ++c) p[(size_t)c * Vs] = make_float4(v[c].re.hi, v[c].im.hi, v[c].re.lo, v[c].im.lo);
     }
 };
 
@@ -348,10 +349,10 @@ template <int RECON> struct LinkIO<DF32, RECON> {
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 float4 t = __ldg(p + (size_t)e * Vs);
-                w[e + 1] = C<double>{(double)t.x + (double)t.y, (double)t.z + (double)t.w};
+                w[e + 1] = C<double>{(double)t.x + (double)t.z, (double)t.y + (double)t.w};
             }
             const float4 th = __ldg(p + (size_t)3 * Vs);
-            rebuild_recon8(w, (double)th.x + (double)th.y, (double)th.z + (double)th.w);
+            rebuild_recon8(w, (double)th.x + (double)th.z, (double)th.y + (double)th.w);
 #pragma unroll
             for (int e = 0; e < 9; ++e) u[e] = C<R>{df(w[e].re), df(w[e].im)};
             return;
@@ -360,7 +361,7 @@ template <int RECON> struct LinkIO<DF32, RECON> {
 #pragma unroll
         for (int e = 0; e < n; ++e) {
             float4 t = __ldg(p + (size_t)e * Vs);
-            u[e] = C<R>{df(t.x, t.y), df(t.z, t.w)};
+            u[e] = C<R>{df(t.x, t.z), df(t.y, t.w)};
         }
         if (RECON == 12) rebuild_row2(u);
     }
