@@ -102,6 +102,69 @@ def recorded_traffic(kernel_key: str):
     return e.get("bytes_per_launch")
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (read-only queries) every
+    10 ms while the timed region runs.  Raises on start if NVML is not usable."""
+
+    # clock-event reason bits of NVML's public header
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index=0, period_s=0.01):
+        import ctypes
+        self.ct = ctypes
+        self.period = period_s
+        self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nvml.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+            ok = self.nvml.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.nvml.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.get_reasons = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples, self.reasons, self.stop_flag = [], 0, False
+
+    def _sm_clock(self, fn):
+        v = self.ct.c_uint()
+        return v.value if fn(self.h, 1, self.ct.byref(v)) == 0 else None  # 1 = NVML_CLOCK_SM
+
+    def _run(self):
+        r = self.ct.c_ulonglong()
+        while not self.stop_flag:
+            c = self._sm_clock(self.nvml.nvmlDeviceGetClockInfo)
+            if c is not None:
+                self.samples.append(c)
+            if self.get_reasons(self.h, self.ct.byref(r)) == 0:
+                self.reasons |= r.value
+            time.sleep(self.period)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        self.thread.join(timeout=5)
+        smax = self._sm_clock(self.nvml.nvmlDeviceGetMaxClockInfo)
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": smax,
+                "reasons": sorted(n for b, n in self.REASONS.items() if self.reasons & b),
+                "samples": len(self.samples), "source": "nvml, 10 ms"}
+
+
+def clock_sampler(index=0):
+    try:
+        return NvmlClockSampler(index)
+    except Exception:
+        return ClockSampler(index)
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples taken while the timed region runs."""
 
@@ -151,7 +214,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -329,7 +392,7 @@ def main():
         solve()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     times, launches, results = [], 0, None
     if dist:

@@ -16,7 +16,7 @@ struct VecArgs {
     Scalars *sc;
     int mask;
     unsigned long long cond;   // while-loop handle to set (0 = none)
-    int *state;                // [0] body iterations, [1] reliable-update bodies run
+    int *state;                // [0] body iterations, [1] reliable-update bodies run, [2] x0 nonzero
 };
 
 template <class T> __device__ __forceinline__ const void *rp(const T *b, size_t st, int r) {
@@ -91,6 +91,21 @@ template <int P> __global__ void k_xpby(VecArgs v) {
 #pragma unroll
     for (int c = 0; c < 12; ++c) y[c] = C<R>{x[c].re + beta * y[c].re, x[c].im + beta * y[c].im};
     SpinorIO<P>::store(pb, v.Vs, s, y);
+}
+
+// state[2] = 1 if the FP64 field a (the start vector x0) has a nonzero (or NaN)
+// component at some site of some row; state[2] is cleared before the solve.
+template <int DUMMY = 0> __global__ void k_any_nonzero(VecArgs v) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (s >= v.V) return;
+    const double2 *p = reinterpret_cast<const double2 *>(rp(v.a, v.a_stride, r)) + s;
+    bool nz = false;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const double2 t = p[(size_t)c * v.Vs];
+        nz |= !(t.x == 0.0) || !(t.y == 0.0);
+    }
+    if (nz) v.state[2] = 1;
 }
 
 // x (F64) += xs (F32); xs = 0, rows with a pending reliable update.  Block (0, 0)

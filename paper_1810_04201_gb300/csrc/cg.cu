@@ -191,7 +191,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
             h[r].status = WD_ERR_NOT_CONVERGED;
         }
         WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
-        WD_CUDA(c, cudaMemsetAsync(f.state, 0, 2 * sizeof(int), c->stream));
+        WD_CUDA(c, cudaMemsetAsync(f.state, 0, 3 * sizeof(int), c->stream));
         EventPair ev;
         WD_CUDA(c, ev.create());
         cudaEvent_t e0 = ev.e0, e1 = ev.e1;

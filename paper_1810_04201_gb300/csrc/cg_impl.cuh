@@ -75,11 +75,21 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
         a.in = f.b; a.out = f.db;
         if (NE) a.kappa = 0.0;  // D with kappa = 0 is the identity: db = b, |b|^2
         add_op<F64, RECON, true, EpSetupDb, EO>(gb, a, pl.t64, true, f);
+        // a zero start vector (the usual case) makes t = OP1 x0 and OP2 t vanish:
+        // state[2] marks a nonzero x0, and without one those kernels do no work
+        VecArgs v = vb;
+        v.mask = 0;
+        v.a = f.x; v.a_stride = s64;
+        gb.kernel(k_any_nonzero<0>, dim3((v.V + 127) / 128, v.nrhs), dim3(128), v);
         a.kappa = pl.kappa;
         a.in = f.x; a.out = f.t;
+        a.run_flag = f.state + 2;
         add_op<F64, RECON, OP1, EpXpay, EO>(gb, a, pl.t64, false, f);
+        a.run_flag = nullptr;
         a.in = f.t; a.a0 = f.db; a.a1 = f.r; a.a2 = f.p;
+        a.in_nonzero = f.state + 2;
         add_op<F64, RECON, OP2, EpSetupR, EO>(gb, a, pl.t64, true, f);
+        a.in_nonzero = nullptr;
     }
     if (mixed) {
         VecArgs v = vb;

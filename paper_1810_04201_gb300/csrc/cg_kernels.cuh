@@ -73,15 +73,21 @@ struct EpSetupDb {
     }
 };
 
-// q = D^dag t; r = db - q (a1), p = r (a2); rho = |r|^2; rows already converged stop
+// q = D^dag t; r = db - q (a1), p = r (a2); rho = |r|^2; rows already converged stop.
+// With a zero start vector (in_nonzero flag 0) t was never formed: q = 0, r = db.
 struct EpSetupR {
     struct State { double v[1]; };
     template <int P, class R, class Pt>
     static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
                                                 State &st, const Pt &pt) {
         C<R> q[Pt::N], d[Pt::N];
-        load_part<P>(pt, in, a.g.Vs, s, q);
-        xpay_site(q, acc, R(a.kappa));
+        if (a.in_nonzero && *a.in_nonzero == 0) {
+#pragma unroll
+            for (int c = 0; c < Pt::N; ++c) q[c] = C<R>{R(0), R(0)};
+        } else {
+            load_part<P>(pt, in, a.g.Vs, s, q);
+            xpay_site(q, acc, R(a.kappa));
+        }
         load_part<P>(pt, rhs_ptr<R>(a.a0, a.a0_stride, r), a.g.Vs, s, d);
 #pragma unroll
         for (int c = 0; c < Pt::N; ++c) d[c] = csub(d[c], q[c]);

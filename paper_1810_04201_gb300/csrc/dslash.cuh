@@ -43,6 +43,7 @@ struct DslashArgs {
     const int *run_flag;       // when set and zero, the whole launch returns at once
     const void *xsrc;          // field added by the xpay epilogues (nullptr: the hopping input)
     size_t xsrc_stride;
+    const int *in_nonzero;     // when set and zero, the input fields are zero: not read, hopping sum 0
 };
 
 template <class R> __device__ __forceinline__ const void *rhs_ptr(const void *b, size_t stride, int r) {
@@ -713,6 +714,7 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
     const void *in = rhs_ptr<R>(a.in, a.in_stride, rr);
     // the field the xpay epilogues add: the hopping input unless another is given
     const void *xin = a.xsrc ? rhs_ptr<R>(a.xsrc, a.xsrc_stride, rr) : in;
+    const bool zin = a.in_nonzero && *a.in_nonzero == 0;
     typename Ep::State st{};
     if constexpr (split_site<P>()) {
         // two lanes per site (blockDim.x a multiple of 32): lane l of warp w of the
@@ -725,7 +727,7 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
             const int s = s0 + sl;
             const bool on = row && s < a.g.V;
             C<R> acc[9];
-            if (on) hopping_half<P, RECON, DAG, EO>(a.g, in, a.gauge, a.gauge_dir, s, hh, acc);
+            if (on && !zin) hopping_half<P, RECON, DAG, EO>(a.g, in, a.gauge, a.gauge_dir, s, hh, acc);
             else
 #pragma unroll
                 for (int k = 0; k < 9; ++k) acc[k] = C<R>{R(0), R(0)};
@@ -743,7 +745,10 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
             const int s = s0 + threadIdx.x;
             if (row && s < a.g.V) {
                 C<R> acc[12];
-                if constexpr (EO) hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
+                if (zin)
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) acc[k] = C<R>{R(0), R(0)};
+                else if constexpr (EO) hopping_eo<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
                 else hopping<P, RECON, DAG>(a.g, in, a.gauge, a.gauge_dir, s, acc);
                 Ep::template site<P>(a, s, r, xin, acc, st, pt);
             }

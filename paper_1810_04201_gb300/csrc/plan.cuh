@@ -168,6 +168,8 @@ static void add_op(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool re
         h.out_stride = sp;
         h.kappa = -1.0;
         h.xsrc = nullptr;
+        // a zero input (in_nonzero flag 0) needs no bare hop: the epilogue kernel skips it too
+        if (a.in_nonzero) h.run_flag = a.in_nonzero, h.in_nonzero = nullptr;
         add_dslash<P, RECON, DAG, EpHop, true>(gb, h, t, false);
         DslashArgs e = a;
         e.g = f.eo.ge;

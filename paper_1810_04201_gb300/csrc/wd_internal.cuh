@@ -519,7 +519,7 @@ __device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
 inline double default_delta(Prec p) {
     switch (p) {
     case F16: return 1e-2;
-    case F32: return 1e-3;
+    case F32: return 1e-4;
     case DF32: return 1e-6;
     default: return 0.1;
     }

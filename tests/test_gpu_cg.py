@@ -112,6 +112,34 @@ def test_cg_initial_guess_and_zero_source(wd):
     assert not lat.unpack(fz).any()
 
 
+@pytest.mark.parametrize("inner,eo", [(0, 0), (1, 0), (0, 1), (2, 1)])
+def test_start_vector_zero_and_nearly_zero(wd, inner, eo):
+    """A zero start vector skips the D x0 work; a start vector with one tiny nonzero
+    entry (and the same vector in another right-hand side) takes the full setup.  All
+    reach the oracle solution."""
+    dims, kappa = (4, 4, 4, 6), 0.12
+    U = gen.haar_links(dims, seed=31)
+    b = gen.gaussian_source(dims, seed=32)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb = lat.pack(b)
+    x0 = np.zeros_like(b)
+    x0[7, 2, 1] = 1e-300
+    for start in (np.zeros_like(b), x0, 0.5 * x_ref):
+        fx = lat.pack(start)
+        res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner, precondition=eo)
+        assert st == 0 and res[0]["true_rel_resid"] <= 1e-10
+        assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+    B = np.stack([b, b])
+    X0 = np.stack([np.zeros_like(b), x0])
+    fX = lat.pack(X0)
+    res, st = lat.cg(kappa, lat.pack(B), fX, tol=1e-10, inner=inner, nrhs=2, precondition=eo)
+    assert st == 0
+    X = lat.unpack(fX, nrhs=2, squeeze=False)
+    assert all(oracle.rel_err(X[j], x_ref) < 1e-9 for j in range(2))
+
+
 def test_cg_failure_statuses(wd):
     dims, kappa = (4, 4, 4, 4), 0.12
     U = gen.haar_links(dims, seed=1)
