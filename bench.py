@@ -309,9 +309,11 @@ METRIC = "Dslash GFLOP/s & HBM GB/s (% roofline); CG time-to-1e-10, mixed/multi-
 def config_of(args, w):
     return {"workload": f"{args.workload}: {'x'.join(map(str, w['dims']))} {w['links']} links, kappa={w['kappa']}, "
                         f"{'12 point sources' if w['nrhs'] == 12 else 'Gaussian source'}, CGNR to true residual "
-                        f"1e-10, inner precision {args.inner or w['inner']}, recon {args.recon}",
+                        f"1e-10, inner precision {args.inner or w['inner']}, recon {args.recon}"
+                        + (f" (inner-precision links recon {args.recon_inner})" if getattr(args, "recon_inner", None) else ""),
             "lattice": list(w["dims"]), "nrhs": w["nrhs"], "kappa": w["kappa"], "tol": 1e-10,
             "inner_prec": args.inner or w["inner"], "recon": args.recon,
+            "recon_inner": getattr(args, "recon_inner", None) or args.recon,
             "preconditioner": "even-odd" if getattr(args, "eo", False) else "none",
             "l2": "flushed (512 MB write) before every timed step and every timed Dslash launch",
             "parallelism": "replicas (one independent lattice per GPU)"}
@@ -326,6 +328,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5"])
     ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--recon", type=int, default=18, choices=[18, 12, 8])
+    ap.add_argument("--recon-inner", type=int, default=None, choices=[18, 12, 8],
+                    help="link compression of the inner precision's copy (default: --recon)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eo", action="store_true", help="even-odd preconditioned solve")
@@ -374,6 +378,8 @@ def main():
     U, b = make_inputs(w, rank)
     lat = wd.Lattice(w["dims"])
     lat.set_gauge(U, recon=args.recon)
+    if args.recon_inner and inner != "f64":
+        lat.set_link_compression(wd.PRECS[inner], args.recon_inner)
     # the autotuner picks the thread-block shape of the Dslash for this lattice
     tuned = {p: lat.autotune(wd.PRECS[p], nrhs) for p in sorted({"f64", inner})}
     fb = lat.pack(b)
@@ -439,7 +445,8 @@ def main():
     clk = clocks.stop()
     d_ms = statistics.mean(dts)
     d_gflops = FLOP_PER_SITE * V * nrhs / (d_ms * 1e-3) / 1e9
-    link_b = LINK_BYTES[(prec, args.recon)]
+    rprec = args.recon_inner if (args.recon_inner and prec != "f64") else args.recon
+    link_b = LINK_BYTES[(prec, rprec)]
     d_bytes = V * (nrhs * 2 * SPINOR_BYTES[prec] + link_b)
     d_gbs = d_bytes / (d_ms * 1e-3) / 1e9
     peaks = load_peaks()
@@ -484,9 +491,9 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(d_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(d_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}
-    kkey = f"dslash_{prec}_r{args.recon}_{'x'.join(map(str, w['dims']))}_nrhs{nrhs}"
+    kkey = f"dslash_{prec}_r{rprec}_{'x'.join(map(str, w['dims']))}_nrhs{nrhs}"
     roof["traffic"] = recorded_traffic(kkey)
-    roof["kernel"] = f"wd::dslash_kernel<{pid},{args.recon},false,EpXpay> ({kkey})"
+    roof["kernel"] = f"wd::dslash_kernel<{pid},{rprec},false,EpXpay> ({kkey})"
     roof["algorithmic_bytes_per_launch"] = d_bytes
     roof["algorithmic_flops_per_launch"] = FLOP_PER_SITE * V * nrhs
     roof["avg_launch_ms"] = round(d_ms, 5)
@@ -587,6 +594,9 @@ def compare(args):
     dims = w["dims"]
     lat = wd.Lattice(dims)
     lat.set_gauge(U, recon=args.recon)
+    if args.recon_inner:
+        for p in (wd.WD_F32, wd.WD_F16, wd.WD_DF32):
+            lat.set_link_compression(p, args.recon_inner)
     V = lat.V
     if args.workload in ("c1", "c2", "c3"):
         fb = lat.pack(b)

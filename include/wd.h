@@ -104,6 +104,18 @@ wd_status wd_set_stream(wd_ctx *ctx, void *stream);
  * operators are derived from the same field when first needed. */
 wd_status wd_set_gauge(wd_ctx *ctx, const double *U_canon, int on_device, int recon);
 
+/* Store the links of one precision with another compression than wd_set_gauge's
+ * (18, 12 or 8, with the recon = 8 condition above).  No counterpart in the paper: on
+ * GB300 the FP64 operator is bound by the FP64 units, so compressed links only add
+ * arithmetic there, while the FP32/FP16 operators are bound by memory and gain from
+ * them; a mixed-precision solve can keep FP64 links whole (18) and compress the inner
+ * precision's (12).  Applies until the next wd_set_gauge, which resets every precision
+ * to its recon.  The solvers accept any compression for the inner precision when the
+ * FP64 links are whole, and otherwise the same compression for both; the batched
+ * solver needs the same compression for both.  Errors: WD_ERR_ARG (bad precision or
+ * recon, links unsuited to recon 8), WD_ERR_STATE (no gauge field yet). */
+wd_status wd_set_link_compression(wd_ctx *ctx, wd_prec prec, int recon);
+
 /* Bytes of one device field of nrhs right-hand sides in precision prec. */
 size_t wd_field_bytes(const wd_ctx *ctx, wd_prec prec, int nrhs);
 

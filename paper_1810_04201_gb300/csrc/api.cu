@@ -43,7 +43,7 @@ wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out) {
     return WD_OK;
 }
 
-size_t gauge_dir_bytes(const wd_ctx *c, Prec p) { return round_up(link_dir_bytes(p, c->recon, c->g.Vs), 256); }
+size_t gauge_dir_bytes(const wd_ctx *c, Prec p) { return round_up(link_dir_bytes(p, link_recon(c, p), c->g.Vs), 256); }
 
 template <int P, int RECON>
 static void gauge_pack(const double *canon, void *dst, const Geom &g, size_t dir, cudaStream_t st) {
@@ -55,9 +55,9 @@ wd_status gauge_get(wd_ctx *c, Prec p, const void **out) {
     if (!c->has_gauge) return fail(c, WD_ERR_STATE, "no gauge field set (call wd_set_gauge first)");
     if (!c->gauge[p]) {
         void *d = nullptr;
-        WD_CUDA(c, cudaMalloc(&d, gauge_bytes(p, c->recon, c->g.Vs)));
+        WD_CUDA(c, cudaMalloc(&d, gauge_bytes(p, link_recon(c, p), c->g.Vs)));
         const size_t dir = gauge_dir_bytes(c, p);
-        with_recon(c->recon, [&](auto rc) {
+        with_recon(link_recon(c, p), [&](auto rc) {
             constexpr int R = decltype(rc)::value;
             if (p == F64) gauge_pack<F64, R>(c->gauge_canon, d, c->g, dir, c->stream);
             else if (p == F32) gauge_pack<F32, R>(c->gauge_canon, d, c->g, dir, c->stream);
@@ -69,6 +69,29 @@ wd_status gauge_get(wd_ctx *c, Prec p, const void **out) {
         c->gauge[p] = d;
     }
     *out = c->gauge[p];
+    return WD_OK;
+}
+
+// The 8-real parametrisation divides by |u01|^2 + |u02|^2 (zero for the unit link):
+// WD_ERR_ARG unless it is at least 1e-6 on every link of the canonical copy.
+wd_status check_recon8(wd_ctx *c, const char *who) {
+    void *w;
+    wd_status s = ws_get(c, "gauge_check", sizeof(unsigned), &w);
+    if (s != WD_OK) return s;
+    WD_CUDA(c, cudaMemsetAsync(w, 0x7f, sizeof(unsigned), c->stream));
+    const size_t nl = (size_t)4 * c->g.V;
+    k_gauge_min_offdiag<<<(int)std::min<size_t>((nl + 255) / 256, 4096), 256, 0, c->stream>>>(
+        reinterpret_cast<const double2 *>(c->gauge_canon), nl, static_cast<unsigned *>(w));
+    WD_CUDA(c, cudaGetLastError());
+    c->launches += 1;
+    unsigned bits = 0;
+    WD_CUDA(c, cudaMemcpyAsync(&bits, w, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+    WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    float nmin;
+    std::memcpy(&nmin, &bits, sizeof nmin);
+    if (!(nmin >= 1e-6f))
+        return fail(c, WD_ERR_ARG, std::string(who) + ": recon 8 needs |U01|^2 + |U02|^2 >= 1e-6 on every link "
+                                   "(smallest: " + std::to_string(nmin) + "); use recon 12 or 18");
     return WD_OK;
 }
 
@@ -89,11 +112,11 @@ static void gauge_pack_eo(const double *canon, void *dst, const Geom &g, int Vhs
 wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes) {
     if (!c->has_gauge) return fail(c, WD_ERR_STATE, "no gauge field set (call wd_set_gauge first)");
     const int Vhs = eo_geom(c, 0).Vs;
-    const size_t dir = round_up(link_dir_bytes(p, c->recon, Vhs), 256);
+    const size_t dir = round_up(link_dir_bytes(p, link_recon(c, p), Vhs), 256);
     if (!c->gauge_eo[p]) {
         void *d = nullptr;
         WD_CUDA(c, cudaMalloc(&d, 8 * dir));
-        with_recon(c->recon, [&](auto rc) {
+        with_recon(link_recon(c, p), [&](auto rc) {
             constexpr int R = decltype(rc)::value;
             if (p == F64) gauge_pack_eo<F64, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
             else if (p == F32) gauge_pack_eo<F32, R>(c->gauge_canon, d, c->g, Vhs, dir, c->stream);
@@ -215,35 +238,41 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     WD_CUDA(c, cudaMemcpyAsync(c->gauge_canon, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                c->stream));
     c->recon = recon;
+    for (int p = 0; p < kNumPrec; ++p) c->recon_p[p] = 0;
     c->has_gauge = false;
     // graphs bake gauge pointers in
     for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
     c->graphs.clear();
     if (recon == 8) {
-        // the 8-real parametrisation divides by |u01|^2 + |u02|^2 (zero for the unit link)
-        void *w;
-        wd_status s = ws_get(c, "gauge_check", sizeof(unsigned), &w);
+        wd_status s = check_recon8(c, "wd_set_gauge");
         if (s != WD_OK) return s;
-        WD_CUDA(c, cudaMemsetAsync(w, 0x7f, sizeof(unsigned), c->stream));
-        const size_t nl = (size_t)4 * c->g.V;
-        k_gauge_min_offdiag<<<(int)std::min<size_t>((nl + 255) / 256, 4096), 256, 0, c->stream>>>(
-            reinterpret_cast<const double2 *>(c->gauge_canon), nl, static_cast<unsigned *>(w));
-        WD_CUDA(c, cudaGetLastError());
-        c->launches += 1;
-        unsigned bits = 0;
-        WD_CUDA(c, cudaMemcpyAsync(&bits, w, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
-        WD_CUDA(c, cudaStreamSynchronize(c->stream));
-        float nmin;
-        std::memcpy(&nmin, &bits, sizeof nmin);
-        if (!(nmin >= 1e-6f))
-            return fail(c, WD_ERR_ARG, "wd_set_gauge: recon 8 needs |U01|^2 + |U02|^2 >= 1e-6 on every link "
-                                       "(smallest: " + std::to_string(nmin) + "); use recon 12 or 18");
     }
     c->has_gauge = true;
     const void *d;
     wd_status s = gauge_get(c, F64, &d);
     if (s != WD_OK) return s;
     if (!on_device) WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WD_OK;
+}
+
+wd_status wd_set_link_compression(wd_ctx *c, wd_prec prec, int recon) {
+    if (!c) return WD_ERR_ARG;
+    if (bad_prec(prec)) return fail(c, WD_ERR_ARG, "wd_set_link_compression: bad precision");
+    if (recon != 18 && recon != 12 && recon != 8)
+        return fail(c, WD_ERR_ARG, "wd_set_link_compression: recon must be 18, 12 or 8");
+    if (!c->has_gauge) return fail(c, WD_ERR_STATE, "no gauge field set (call wd_set_gauge first)");
+    if (recon == link_recon(c, (Prec)prec)) return WD_OK;
+    if (recon == 8) {
+        wd_status s = check_recon8(c, "wd_set_link_compression");
+        if (s != WD_OK) return s;
+    }
+    WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->gauge[prec]) cudaFree(c->gauge[prec]);
+    if (c->gauge_eo[prec]) cudaFree(c->gauge_eo[prec]);
+    c->gauge[prec] = c->gauge_eo[prec] = nullptr;
+    c->recon_p[prec] = recon;
+    for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
+    c->graphs.clear();
     return WD_OK;
 }
 
@@ -337,7 +366,7 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
     a.gauge_dir = gauge_dir_bytes(c, (Prec)prec);
     a.kappa = kappa;
     a.nrhs = nrhs;
-    WD_CUDA(c, launch_apply(a, (Prec)prec, c->recon, dagger, tiles_for(c, (Prec)prec, nrhs), c->stream));
+    WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, tiles_for(c, (Prec)prec, nrhs), c->stream));
     c->launches += 1;
     return WD_OK;
 }

@@ -71,9 +71,9 @@ wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rh
             DslashTiles t;
             t.site_tile = st;
             t.rhs_tile = rt;
-            for (int k = 0; k < 2; ++k) WD_CUDA(c, launch_apply(a, (Prec)prec, c->recon, false, t, c->stream));
+            for (int k = 0; k < 2; ++k) WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), false, t, c->stream));
             WD_CUDA(c, cudaEventRecord(e0, c->stream));
-            for (int k = 0; k < 5; ++k) WD_CUDA(c, launch_apply(a, (Prec)prec, c->recon, false, t, c->stream));
+            for (int k = 0; k < 5; ++k) WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), false, t, c->stream));
             WD_CUDA(c, cudaEventRecord(e1, c->stream));
             WD_CUDA(c, cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -449,7 +449,9 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
         if (!c || !b[i] || !x[i] || !std::isfinite(kappas[i]))
             return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: null context, field or bad kappa");
         if (c->device != c0->device) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: contexts on different devices");
-        if (c->recon != c0->recon) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: mixed link compression");
+        if (link_recon(c, F64) != link_recon(c0, F64) || link_recon(c, sp) != link_recon(c, F64))
+            return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: every context needs one link compression for FP64 "
+                                        "and the inner precision");
         wd_status s;
         const void *g64, *gs;
         if ((s = gauge_get(c, F64, &g64)) != WD_OK) return fail(c0, s, c->last_error);
@@ -525,14 +527,14 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     a.spin_limit = a.stall_test ? 200000000ll : 2000000000ll;
 
     char key[160];
-    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p|%p", (int)sp, c0->recon, n, ntiles, prm->max_iter,
+    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p|%p", (int)sp, link_recon(c0, F64), n, ntiles, prm->max_iter,
              a.stall_test, d_part, d_lat);
     cudaGraphExec_t exec;
     auto it = c0->graphs.find(key);
     if (it != c0->graphs.end()) {
         exec = (cudaGraphExec_t)it->second;
     } else {
-        const cudaError_t e = with_recon(c0->recon, [&](auto rc) {
+        const cudaError_t e = with_recon(link_recon(c0, F64), [&](auto rc) {
             constexpr int R = decltype(rc)::value;
             return sp == F32 ? build_batched<F32, R>(a, &exec) : build_batched<F16, R>(a, &exec);
         });

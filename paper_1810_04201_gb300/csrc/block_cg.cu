@@ -355,7 +355,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
 
     const DslashTiles t64 = tiles_for(c, F64, k);
     char key[200];
-    snprintf(key, sizeof key, "bcg|%d|%d|%a|%d,%d", k, c->recon, kappa, t64.site_tile, t64.rhs_tile);
+    snprintf(key, sizeof key, "bcg|%d|%d|%a|%d,%d", k, link_recon(c, F64), kappa, t64.site_tile, t64.rhs_tile);
     cudaGraphExec_t exec;
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
@@ -366,7 +366,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
         cudaGraphConditionalHandle hw = 0;
         cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault);
         Plan plan;
-        with_recon(c->recon, [&](auto rc) { record_block<decltype(rc)::value>(c, kappa, k, g64, f, hw, plan); });
+        with_recon(link_recon(c, F64), [&](auto rc) { record_block<decltype(rc)::value>(c, kappa, k, g64, f, hw, plan); });
         std::vector<cudaGraphNode_t> deps;
         if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
         cudaGraph_t body = nullptr;

@@ -17,12 +17,21 @@ using namespace wd;
 
 namespace wd {
 
-// Solver plans per link compression, instantiated in cg_recon{18,12,8}.cu.
-template <int RECON>
+// Solver plans per pair of link compressions (FP64, inner precision), instantiated in
+// cg_recon18.cu, cg_recon12.cu, cg_recon8.cu, cg_recon18_12.cu and cg_recon18_8.cu.
+template <int RECON, int RIN>
 cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                       cudaGraphExec_t *exec, std::vector<long long> &counts);
-template <int RECON>
+template <int RECON, int RIN>
 void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan);
+
+// Calls fn(integral_constant<R64>, integral_constant<RIN>) for the built pairs.
+template <class F> static decltype(auto) with_recon_pair(int r64, int rin, F &&fn) {
+    using std::integral_constant;
+    if (r64 == 18 && rin == 12) return fn(integral_constant<int, 18>{}, integral_constant<int, 12>{});
+    if (r64 == 18 && rin == 8) return fn(integral_constant<int, 18>{}, integral_constant<int, 8>{});
+    return with_recon(r64, [&](auto rc) { return fn(rc, rc); });
+}
 
 // The same plan launched kernel by kernel from the host; the active flags are read
 // back every `chunk` iterations.  Loop kernels of converged rows return at once,
@@ -139,24 +148,30 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     f.counter = (unsigned *)tmp;
     f.state = (int *)((char *)tmp + 64);
 
-    SolverPlan pl{c->recon, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs),
+    const int r64 = link_recon(c, F64), rin = inner == F64 ? r64 : link_recon(c, inner);
+    if (rin != r64 && r64 != 18)
+        return fail(c, WD_ERR_ARG, "wd_cg_solve: with compressed FP64 links the inner precision needs the same "
+                                   "compression (see wd_set_link_compression)");
+    SolverPlan pl{r64, rin, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs),
                   prm->normal_eq ? 1 : 0, eo ? 1 : 0};
     char key[256];
-    snprintf(key, sizeof key, "cg|%d|%d|%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, c->recon, kappa, pl.t64.site_tile,
+    snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, r64, rin, kappa, pl.t64.site_tile,
              pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo);
     const char *loop_env = getenv("WD_CG_LOOP");
     const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
     cudaGraphExec_t exec = nullptr;
     Plan hplan;
     if (host_loop) {
-        with_recon(c->recon, [&](auto rc) { record_for<decltype(rc)::value>(c, pl, f, g64, gin, hplan); });
+        with_recon_pair(r64, rin, [&](auto ra, auto rb) {
+            record_for<decltype(ra)::value, decltype(rb)::value>(c, pl, f, g64, gin, hplan);
+        });
         WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 64, c->stream));
     } else {
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             std::vector<long long> counts;
-            cudaError_t e = with_recon(c->recon, [&](auto rc) {
-                return build_for<decltype(rc)::value>(c, pl, f, g64, gin, &exec, counts);
+            cudaError_t e = with_recon_pair(r64, rin, [&](auto ra, auto rb) {
+                return build_for<decltype(ra)::value, decltype(rb)::value>(c, pl, f, g64, gin, &exec, counts);
             });
             if (e != cudaSuccess) return cuda_fail(c, e, "building the CG graph");
             c->graphs[key] = exec;

@@ -1,8 +1,9 @@
 // Solver plans of the device-resident CG (section 2.2): the recording of every
 // kernel of one solve for a given link compression, inner precision, normal form
 // and preconditioning, and its assembly into a CUDA graph with device-side loop.
-// Each link compression is instantiated in its own translation unit
-// (cg_recon18.cu, cg_recon12.cu, cg_recon8.cu), which keeps the build parallel.
+// Each pair of link compressions (FP64, inner precision) is instantiated in its own
+// translation unit (cg_recon18.cu, cg_recon12.cu, cg_recon8.cu, cg_recon18_12.cu,
+// cg_recon18_8.cu), which keeps the build parallel.
 #pragma once
 #include <vector>
 #include "cg_kernels.cuh"
@@ -18,7 +19,7 @@ namespace wd {
 // The two share every kernel; only which of D and D^dag comes first changes.
 // EO = true: even-odd preconditioning; the iteration runs on the even half with
 // the Schur operator, the odd half is rebuilt at the end (CGNR only).
-template <int RECON, int SP, bool NE, bool EO>
+template <int RECON, int RIN, int SP, bool NE, bool EO>
 static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                         cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif, Plan &plan) {
     static_assert(!(NE && EO), "even-odd preconditioning is built for CGNR");
@@ -124,9 +125,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
             a.in_stride = a.out_stride = a.a0_stride = a.a1_stride = sin;
             a.a2_stride = s32;
             a.in = f.ps; a.out = f.ts;
-            add_op<SP, RECON, OP1, EpCG1, EO>(bb, a, pl.tin, true, f);
+            add_op<SP, RIN, OP1, EpCG1, EO>(bb, a, pl.tin, true, f);
             a.in = f.ts; a.a0 = f.ps; a.a1 = f.rs; a.a2 = f.xs; a.cond = hif;
-            add_op<SP, RECON, OP2, EpCG2Mixed, EO>(bb, a, pl.tin, true, f);
+            add_op<SP, RIN, OP2, EpCG2Mixed, EO>(bb, a, pl.tin, true, f);
             plan.has_if = true;
             {
                 GraphBuilder ib(&plan.ifb);
@@ -199,7 +200,7 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
 }
 
 // One CUDA graph: setup -> WHILE { pre -> IF { ifb } -> post } -> final.
-template <int RECON, int SP, bool NE, bool EO>
+template <int RECON, int RIN, int SP, bool NE, bool EO>
 static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                                cudaGraphExec_t *exec, std::vector<long long> &counts) {
     cudaGraph_t graph;
@@ -209,7 +210,7 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     e = cudaGraphConditionalHandleCreate(&hwhile, graph, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && SP != F64) e = cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault);
     Plan plan;
-    if (e == cudaSuccess) record_plan<RECON, SP, NE, EO>(c, pl, f, g64, gin, hwhile, hif, plan);
+    if (e == cudaSuccess) record_plan<RECON, RIN, SP, NE, EO>(c, pl, f, g64, gin, hwhile, hif, plan);
     std::vector<cudaGraphNode_t> deps;
     if (e == cudaSuccess) e = add_chain(graph, deps, plan.setup);
     cudaGraph_t body = nullptr;
@@ -233,41 +234,47 @@ static cudaError_t build_graph(wd_ctx *c, const SolverPlan &pl, const Fields &f,
     return e;
 }
 
-template <int RECON, bool NE, bool EO>
+// RIN: link compression of the inner precision; a plain FP64 solve has none of its own
+// (RIN == RECON), a mixed one may keep whole FP64 links (RECON == 18) beside any RIN.
+template <int RECON, int RIN, bool NE, bool EO>
 static cudaError_t build_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                                 cudaGraphExec_t *exec, std::vector<long long> &counts) {
     switch (pl.inner) {
-    case F64: return build_graph<RECON, F64, NE, EO>(c, pl, f, g64, gin, exec, counts);
-    case F32: return build_graph<RECON, F32, NE, EO>(c, pl, f, g64, gin, exec, counts);
-    case DF32: return build_graph<RECON, DF32, NE, EO>(c, pl, f, g64, gin, exec, counts);
-    default: return build_graph<RECON, F16, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case F64:
+        if constexpr (RIN == RECON) return build_graph<RECON, RIN, F64, NE, EO>(c, pl, f, g64, gin, exec, counts);
+        else return cudaErrorInvalidValue;
+    case F32: return build_graph<RECON, RIN, F32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    case DF32: return build_graph<RECON, RIN, DF32, NE, EO>(c, pl, f, g64, gin, exec, counts);
+    default: return build_graph<RECON, RIN, F16, NE, EO>(c, pl, f, g64, gin, exec, counts);
     }
 }
 
-template <int RECON>
+template <int RECON, int RIN>
 cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                              cudaGraphExec_t *exec, std::vector<long long> &counts) {
-    if (pl.eo) return build_for_ne<RECON, false, true>(c, pl, f, g64, gin, exec, counts);
-    return pl.ne ? build_for_ne<RECON, true, false>(c, pl, f, g64, gin, exec, counts)
-                 : build_for_ne<RECON, false, false>(c, pl, f, g64, gin, exec, counts);
+    if (pl.eo) return build_for_ne<RECON, RIN, false, true>(c, pl, f, g64, gin, exec, counts);
+    return pl.ne ? build_for_ne<RECON, RIN, true, false>(c, pl, f, g64, gin, exec, counts)
+                 : build_for_ne<RECON, RIN, false, false>(c, pl, f, g64, gin, exec, counts);
 }
 
-template <int RECON, bool NE, bool EO>
+template <int RECON, int RIN, bool NE, bool EO>
 static void record_for_ne(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin,
                           Plan &plan) {
     switch (pl.inner) {
-    case F64: record_plan<RECON, F64, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case F32: record_plan<RECON, F32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
-    case DF32: record_plan<RECON, DF32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
-    default: record_plan<RECON, F16, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case F64:
+        if constexpr (RIN == RECON) record_plan<RECON, RIN, F64, NE, EO>(c, pl, f, g64, gin, 0, 0, plan);
+        break;
+    case F32: record_plan<RECON, RIN, F32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    case DF32: record_plan<RECON, RIN, DF32, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
+    default: record_plan<RECON, RIN, F16, NE, EO>(c, pl, f, g64, gin, 0, 0, plan); break;
     }
 }
 
-template <int RECON>
+template <int RECON, int RIN>
 void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan) {
-    if (pl.eo) record_for_ne<RECON, false, true>(c, pl, f, g64, gin, plan);
-    else if (pl.ne) record_for_ne<RECON, true, false>(c, pl, f, g64, gin, plan);
-    else record_for_ne<RECON, false, false>(c, pl, f, g64, gin, plan);
+    if (pl.eo) record_for_ne<RECON, RIN, false, true>(c, pl, f, g64, gin, plan);
+    else if (pl.ne) record_for_ne<RECON, RIN, true, false>(c, pl, f, g64, gin, plan);
+    else record_for_ne<RECON, RIN, false, false>(c, pl, f, g64, gin, plan);
 }
 
 }  // namespace wd

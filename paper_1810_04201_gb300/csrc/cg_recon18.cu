@@ -2,7 +2,7 @@
 #include "cg_impl.cuh"
 
 namespace wd {
-template cudaError_t build_for<18>(wd_ctx *, const SolverPlan &, const Fields &, const void *, const void *,
-                                    cudaGraphExec_t *, std::vector<long long> &);
-template void record_for<18>(wd_ctx *, const SolverPlan &, const Fields &, const void *, const void *, Plan &);
+template cudaError_t build_for<18, 18>(wd_ctx *, const SolverPlan &, const Fields &, const void *, const void *,
+                                         cudaGraphExec_t *, std::vector<long long> &);
+template void record_for<18, 18>(wd_ctx *, const SolverPlan &, const Fields &, const void *, const void *, Plan &);
 }  // namespace wd

@@ -60,7 +60,7 @@ extern "C" wd_status wd_apply_schur(wd_ctx *c, double kappa, const void *in, voi
     b.out = oe;
     b.kappa = kappa * kappa;
     const DslashTiles t = tiles_for(c, F64, 1);
-    const cudaError_t err = with_recon(c->recon, [&](auto rc) {
+    const cudaError_t err = with_recon(link_recon(c, F64), [&](auto rc) {
         constexpr int R = decltype(rc)::value;
         return dagger ? schur<R, true>(h, b, t, c->stream) : schur<R, false>(h, b, t, c->stream);
     });

@@ -79,10 +79,10 @@ extern "C" wd_status wd_normal_apply_noalloc(wd_ctx *c, double kappa, const void
     const DslashTiles t = tiles_for(c, (Prec)prec, nrhs);
     a.in = in;
     a.out = tmp;
-    WD_CUDA(c, launch_apply(a, (Prec)prec, c->recon, false, t, c->stream));
+    WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), false, t, c->stream));
     a.in = tmp;
     a.out = out;
-    WD_CUDA(c, launch_apply(a, (Prec)prec, c->recon, true, t, c->stream));
+    WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), true, t, c->stream));
     c->launches = 2;
     return WD_OK;
 }

@@ -140,7 +140,8 @@ static void add_vec(GraphBuilder &gb, K k, const VecArgs &v) {
 }
 
 struct SolverPlan {
-    int recon;
+    int recon;      // link compression of the FP64 copy
+    int recon_in;   // and of the inner precision's copy
     double kappa;
     int nrhs;
     Prec inner;

@@ -54,6 +54,9 @@ template <class F> decltype(auto) with_recon(int recon, F &&f) {
     return f(std::integral_constant<int, 18>{});
 }
 
+// WD_ERR_ARG unless every link suits the 8-real parametrisation (see wd_set_gauge)
+wd_status check_recon8(wd_ctx *c, const char *who);
+
 // workspace: named device buffer of at least `bytes` (kept across calls)
 wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);
 // device gauge field of precision p at the context's recon (created on first use)

@@ -534,7 +534,8 @@ struct wd_ctx {
     wd::Geom g;
     cudaStream_t stream = nullptr;
     int device = 0;
-    int recon = 18;
+    int recon = 18;                                    // link compression set by wd_set_gauge
+    int recon_p[wd::kNumPrec] = {};                    // per-precision overrides (0: recon)
     bool has_gauge = false;
     void *gauge[wd::kNumPrec] = {};                    // per precision (at this->recon)
     void *gauge_eo[wd::kNumPrec] = {};                 // checkerboard copies, per precision
@@ -549,3 +550,9 @@ struct wd_ctx {
     std::map<int, wd::DslashTiles> tiles;              // key: prec*64 + nrhs
     ~wd_ctx();
 };
+
+namespace wd {
+// link compression of the copy of precision p
+inline int link_recon(const wd_ctx *c, Prec p) { return c->recon_p[p] ? c->recon_p[p] : c->recon; }
+}  // namespace wd
+

@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH):
         "wd_destroy": ([P], I),
         "wd_set_stream": ([P, P], I),
         "wd_set_gauge": ([P, P, I, I], I),
+        "wd_set_link_compression": ([P, I, I], I),
         "wd_field_bytes": ([P, I, I], S),
         "wd_pack": ([P, P, I, P, I, I], I),
         "wd_unpack": ([P, P, I, I, P, I], I),
@@ -108,6 +109,7 @@ class Lattice:
         self.V = int(np.prod(self.dims))
         self.ctx = ctypes.c_void_p()
         self.recon = 18
+        self.recon_p = {}
         d = (ctypes.c_int * 4)(*self.dims)
         st = self.lib.wd_create(ctypes.byref(self.ctx), d, int(bool(antiperiodic_t)), _stream_ptr(stream))
         if st != 0:
@@ -158,6 +160,12 @@ class Lattice:
             self._check(self.lib.wd_set_gauge(self.ctx, a.ctypes.data_as(ctypes.c_void_p), 0, recon),
                         "wd_set_gauge")
         self.recon = int(recon)
+        self.recon_p = {}
+
+    def set_link_compression(self, prec, recon):
+        """Store the links of one precision with recon 18, 12 or 8 (until the next set_gauge)."""
+        self._check(self.lib.wd_set_link_compression(self.ctx, prec, recon), "wd_set_link_compression")
+        self.recon_p[int(prec)] = int(recon)
 
     def pack(self, psi, prec=WD_F64, out=None):
         """Canonical spinor(s) (numpy or cuda complex128, (V,4,3) or (nrhs,V,4,3)) -> field."""
@@ -249,7 +257,7 @@ class Lattice:
         path = cache or os.environ.get("WD_TILE_CACHE")
         key = None
         if path:
-            key = tile_cache_key(self.dims, prec, self.recon, nrhs, device_tag())
+            key = tile_cache_key(self.dims, prec, self.recon_p.get(int(prec), self.recon), nrhs, device_tag())
             hit = TileCache(path).get(key)
             if hit is not None:
                 self.set_tiles(prec, nrhs, *hit)

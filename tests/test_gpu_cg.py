@@ -377,3 +377,57 @@ def test_autotune_cache_file(wd, tmp_path):
     assert lat2.autotune(1, 4, cache=path) == t1
     assert lat2.launches == before  # no timing launches
     assert lat2.autotune(1, 2, cache=path) != () and len(json.loads(path.read_text())) == 2
+
+
+@pytest.mark.parametrize("inner,rin,eo", [(1, 12, 1), (2, 8, 0), (1, 8, 1), (3, 12, 0)])
+def test_whole_fp64_links_with_compressed_inner_links(wd, inner, rin, eo):
+    """FP64 links kept whole (18) beside recon-12/8 links of the inner precision: the
+    operators of both precisions and the mixed solve agree with the oracle."""
+    dims, kappa = (4, 6, 4, 8), 0.124
+    U = gen.haar_links(dims, seed=41)
+    b = gen.gaussian_source(dims, seed=42)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=18)
+    lat.set_link_compression(inner, rin)
+    tol = {1: 2e-6, 2: 4e-3, 3: 1e-13}[inner]
+    for prec, t in ((0, 1e-13), (inner, tol)):
+        o = lat.new_field(prec)
+        lat.apply(kappa, lat.pack(b, prec), o, prec)
+        assert oracle.rel_err(lat.unpack(o, prec), oracle.apply_D(U, b, kappa, dims)) < t
+    fx = lat.new_field()
+    res, st = lat.cg(kappa, lat.pack(b), fx, tol=1e-10, inner=inner, precondition=eo)
+    assert st == 0 and res[0]["true_rel_resid"] <= 1e-10
+    assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+
+
+def test_link_compression_rules(wd):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = gen.haar_links(dims, seed=43)
+    b = gen.gaussian_source(dims, seed=44)
+    lat = wd.Lattice(dims)
+    with pytest.raises(wd.WDError) as e:
+        lat.set_link_compression(1, 12)  # no gauge field yet
+    assert e.value.status == 8
+    lat.set_gauge(U, recon=12)
+    with pytest.raises(wd.WDError) as e:
+        lat.set_link_compression(1, 10)
+    assert e.value.status == 1
+    lat.set_link_compression(1, 18)  # compressed FP64 links with whole inner links: refused by the solver
+    res, st = lat.cg(kappa, lat.pack(b), lat.new_field(), tol=1e-10, inner=1, raise_on_fail=False)
+    assert st == 1
+    res, st = lat.cg(kappa, lat.pack(b), lat.new_field(), tol=1e-10, inner=0)  # plain FP64 is fine
+    assert st == 0
+    res, st = wd.cg_batched([lat], [kappa], [lat.pack(b)], [lat.new_field()], tol=1e-10, inner=1)
+    assert st == 1
+    lat.set_gauge(U, recon=12)  # resets every precision
+    assert lat.cg(kappa, lat.pack(b), lat.new_field(), tol=1e-10, inner=1)[1] == 0
+    ul = wd.Lattice(dims)
+    ul.set_gauge(gen.unit_links(dims))
+    with pytest.raises(wd.WDError) as e:
+        ul.set_link_compression(1, 8)
+    assert e.value.status == 1
+    ul.set_link_compression(1, 12)
+    o = ul.new_field(1)
+    ul.apply(kappa, ul.pack(b, 1), o, 1)
+    assert oracle.rel_err(ul.unpack(o, 1), oracle.apply_D(gen.unit_links(dims), b, kappa, dims)) < 2e-6
