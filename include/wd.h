@@ -104,6 +104,17 @@ wd_status wd_set_stream(wd_ctx *ctx, void *stream);
  * operators are derived from the same field when first needed. */
 wd_status wd_set_gauge(wd_ctx *ctx, const double *U_canon, int on_device, int recon);
 
+/* Debug builds (libwd compiled with -DWD_DEBUG; the library's tests build one in
+ * paper_1810_04201_gb300/_build_debug/): every neighbour and checkerboard index a
+ * Dslash kernel of this context computes is checked against its field, and the first
+ * one out of range is kept as 0x80000000 | code << 24 | (index & 0xffffff) (code 1/2:
+ * forward/backward neighbour, 3/4: the same on the checkerboard, 5: checkerboard site)
+ * while the access goes to index 0 instead.  Writes that word to *word (0: none) and
+ * clears it; *is_debug (may be NULL) = 1 for a debug build.  Release builds check
+ * nothing and report 0.  No counterpart in the paper: it stands in for a memory
+ * checker.  Synchronises the context's stream. */
+wd_status wd_debug_word(wd_ctx *ctx, unsigned *word, int *is_debug);
+
 /* Store the links of one precision with another compression than wd_set_gauge's
  * (18, 12 or 8, with the recon = 8 condition above).  No counterpart in the paper: on
  * GB300 the FP64 operator is bound by the FP64 units, so compressed links only add

@@ -14,8 +14,10 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD, "libwd.so")
+BUILD_RELEASE = os.path.join(HERE, "_build")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB = os.path.join(BUILD_RELEASE, "libwd.so")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libwd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]
@@ -39,7 +41,13 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=None, jobs: int | None = None) -> str:
+def build(verbose: bool = False, extra_flags=None, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile (what is stale) and link; debug=True builds the index-checking variant
+    (-DWD_DEBUG) into _build_debug/libwd.so instead."""
+    BUILD = BUILD_DEBUG if debug else BUILD_RELEASE
+    LIB = os.path.join(BUILD, "libwd.so")
+    if debug:
+        extra_flags = list(extra_flags or []) + ["-DWD_DEBUG"]
     os.makedirs(BUILD, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         [os.path.join(os.path.dirname(HERE), "include", "wd.h")]

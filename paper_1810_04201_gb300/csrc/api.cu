@@ -151,6 +151,7 @@ wd_ctx::~wd_ctx() {
         if (gauge_eo[p]) cudaFree(gauge_eo[p]);
     }
     if (gauge_canon) cudaFree(gauge_canon);
+    if (g.dbg) cudaFree(g.dbg);
 }
 
 static bool bad_prec(int p) { return p < 0 || p >= kNumPrec; }
@@ -195,11 +196,18 @@ wd_status wd_create(wd_ctx **out, const int dims[4], int antiperiodic_t, void *s
     c->g.stride[3] = dims[0] * dims[1] * dims[2];
     c->g.antiperiodic = antiperiodic_t ? 1 : 0;
     c->g.eo_parity = -1;
+    c->g.dbg = nullptr;
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
         return WD_ERR_CUDA;
     }
+#ifdef WD_DEBUG
+    if (cudaMalloc(&c->g.dbg, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->g.dbg, 0, sizeof(unsigned)) != cudaSuccess) {
+        delete c;
+        return WD_ERR_CUDA;
+    }
+#endif
     *out = c;
     return WD_OK;
 }
@@ -252,6 +260,20 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     wd_status s = gauge_get(c, F64, &d);
     if (s != WD_OK) return s;
     if (!on_device) WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return WD_OK;
+}
+
+wd_status wd_debug_word(wd_ctx *c, unsigned *word, int *is_debug) {
+    if (!c || !word) return WD_ERR_ARG;
+    *word = 0;
+#ifdef WD_DEBUG
+    if (is_debug) *is_debug = 1;
+    WD_CUDA(c, cudaStreamSynchronize(c->stream));
+    WD_CUDA(c, cudaMemcpy(word, c->g.dbg, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    WD_CUDA(c, cudaMemset(c->g.dbg, 0, sizeof(unsigned)));
+#else
+    if (is_debug) *is_debug = 0;
+#endif
     return WD_OK;
 }
 

@@ -139,7 +139,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF gamma
     const int L = g.L[MU], st = g.stride[MU];
     {
-        const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+        const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
         C<R> p[12], h[6], w[6], u[9];
         SpinorIO<P>::template load<NC>(in, g.Vs, sf, p);
         project<MU, SF>(p, h);
@@ -148,7 +148,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
         accumulate<MU, SF>(acc, w);
     }
     {
-        const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+        const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
         C<R> p[12], h[6], w[6], u[9];
         SpinorIO<P>::template load<NC>(in, g.Vs, sb, p);
         project<MU, -SF>(p, h);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void hop_dir_scaled(const Geom &g, const void *in, co
     constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
     {
-        const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
+        const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
         C<R> p[12], h[6], w[6], u[9];
         const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sf, p);
         project<MU, SF>(p, h);
@@ -176,7 +176,7 @@ __device__ __forceinline__ void hop_dir_scaled(const Geom &g, const void *in, co
         accumulate<MU, SF>(acc, w);
     }
     {
-        const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+        const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
         C<R> p[12], h[6], w[6], u[9];
         const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sb, p);
         project<MU, -SF>(p, h);
@@ -234,7 +234,7 @@ __device__ __forceinline__ int eo_full_index(const Geom &g, int k, int &x, int &
     z = r % g.L[2];
     t = r / g.L[2];
     x = 2 * xh + ((g.eo_parity + y + z + t) & 1);
-    return x + g.stride[1] * y + g.stride[2] * z + g.stride[3] * t;
+    return WD_IDX(g, x + g.stride[1] * y + g.stride[2] * z + g.stride[3] * t, 2 * g.V, 5);
 }
 
 template <int P, int RECON, bool DAG, int MU, bool NC = true>
@@ -244,7 +244,7 @@ __device__ __forceinline__ void hop_dir_eo(const Geom &g, const void *in, const 
     constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
     {
-        const int nf = (c == L - 1) ? n - (L - 1) * st : n + st;
+        const int nf = WD_IDX(g, (c == L - 1) ? n - (L - 1) * st : n + st, 2 * g.V, 3);
         C<R> p[12], h[6], w[6], u[9];
         SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, p);
         project<MU, SF>(p, h);
@@ -253,7 +253,7 @@ __device__ __forceinline__ void hop_dir_eo(const Geom &g, const void *in, const 
         accumulate<MU, SF>(acc, w);
     }
     {
-        const int nb = (c == 0) ? n + (L - 1) * st : n - st;
+        const int nb = WD_IDX(g, (c == 0) ? n + (L - 1) * st : n - st, 2 * g.V, 4);
         C<R> p[12], h[6], w[6], u[9];
         SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, p);
         project<MU, -SF>(p, h);
@@ -420,8 +420,8 @@ template <int P, int RECON, bool DAG, int MU, bool NC, class R>
 __device__ __forceinline__ void half_dir(const Geom &g, const void *in, const char *gdir, int s, int c, int hh,
                                          C<R> (&acc)[9]) {
     const int L = g.L[MU], st = g.stride[MU];
-    const int sf = (c == L - 1) ? s - (L - 1) * st : s + st;
-    const int sb = (c == 0) ? s + (L - 1) * st : s - st;
+    const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
+    const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
     half_pair<P, RECON, DAG, MU < 2 ? 3 : 6, NC>(MU, in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1,
                                                 sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc);
 }
@@ -430,8 +430,8 @@ template <int P, int RECON, bool DAG, int MU, bool NC, class R>
 __device__ __forceinline__ void half_dir_eo(const Geom &g, const void *in, const char *gp, const char *gq, int k,
                                             int n, int c, int hh, C<R> (&acc)[9]) {
     const int L = g.L[MU], st = g.stride[MU];
-    const int nf = (c == L - 1) ? n - (L - 1) * st : n + st;
-    const int nb = (c == 0) ? n + (L - 1) * st : n - st;
+    const int nf = WD_IDX(g, (c == L - 1) ? n - (L - 1) * st : n + st, 2 * g.V, 3);
+    const int nb = WD_IDX(g, (c == 0) ? n + (L - 1) * st : n - st, 2 * g.V, 4);
     half_pair<P, RECON, DAG, MU < 2 ? 3 : 6, NC>(MU, in, g.Vs, nf >> 1, gp, k, MU == 3 && g.antiperiodic && c == L - 1,
                                                 nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, hh, acc);
 }
@@ -554,8 +554,8 @@ __device__ __forceinline__ void half_rolled(const Geom &g, const void *in, const
         const int L = g.L[mu], st = g.stride[mu];
         const int c = mu == 0 ? xc[0] : mu == 1 ? xc[1] : mu == 2 ? xc[2] : xc[3];  // no indexed register array
         const int m = EO ? n : s;
-        const int nf = (c == L - 1) ? m - (L - 1) * st : m + st;
-        const int nb = (c == 0) ? m + (L - 1) * st : m - st;
+        const int nf = WD_IDX(g, (c == L - 1) ? m - (L - 1) * st : m + st, EO ? 2 * g.V : g.V, EO ? 3 : 1);
+        const int nb = WD_IDX(g, (c == 0) ? m + (L - 1) * st : m - st, EO ? 2 * g.V : g.V, EO ? 4 : 2);
         const bool ff = mu == 3 && g.antiperiodic && c == L - 1, fb = mu == 3 && g.antiperiodic && c == 0;
         const char *gf = gp + (size_t)mu * gdir_bytes, *gb = gq + (size_t)mu * gdir_bytes;
         if (EO) half_pair_cd<RECON, DAG, LO, NC>(mu, in, g.Vs, nf >> 1, gf, s, ff, nb >> 1, gb, nb >> 1, fb, hh, acc);

@@ -77,7 +77,23 @@ struct Geom {
     int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz (full-lattice strides)
     int antiperiodic;
     int eo_parity;   // -1: full lattice; 0 / 1: checkerboard fields, output on this parity
+    unsigned *dbg;   // debug builds: the context's word for the first out-of-range index
 };
+
+// Index checks of debug builds (compiled with -DWD_DEBUG, in place of a memory checker):
+// an index outside [0, n) is recorded in the context's debug word, the first one only, as
+// 0x80000000 | code << 24 | (index & 0xffffff), and replaced by 0, so that the access
+// stays inside the field.  Release builds compile the check away.
+#ifdef WD_DEBUG
+__device__ __forceinline__ int checked_index(const Geom &g, int i, int n, unsigned code) {
+    if (i >= 0 && i < n) return i;
+    if (g.dbg) atomicCAS(g.dbg, 0u, 0x80000000u | (code << 24) | ((unsigned)i & 0xffffffu));
+    return 0;
+}
+#define WD_IDX(g, i, n, code) ::wd::checked_index((g), (i), (n), (code))
+#else
+#define WD_IDX(g, i, n, code) (i)
+#endif
 
 // ------------------------------------------------------------------ field sizes
 inline size_t spinor_bytes(Prec p, int Vs) {

@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH):
         "wd_set_stream": ([P, P], I),
         "wd_set_gauge": ([P, P, I, I], I),
         "wd_set_link_compression": ([P, I, I], I),
+        "wd_debug_word": ([P, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(I)], I),
         "wd_field_bytes": ([P, I, I], S),
         "wd_pack": ([P, P, I, P, I, I], I),
         "wd_unpack": ([P, P, I, I, P, I], I),
@@ -161,6 +162,12 @@ class Lattice:
                         "wd_set_gauge")
         self.recon = int(recon)
         self.recon_p = {}
+
+    def debug_word(self):
+        """(first out-of-range index record or 0, debug build?) -- see wd_debug_word."""
+        w, d = ctypes.c_uint(), ctypes.c_int()
+        self._check(self.lib.wd_debug_word(self.ctx, ctypes.byref(w), ctypes.byref(d)), "wd_debug_word")
+        return w.value, bool(d.value)
 
     def set_link_compression(self, prec, recon):
         """Store the links of one precision with recon 18, 12 or 8 (until the next set_gauge)."""
