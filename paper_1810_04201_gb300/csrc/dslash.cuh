@@ -212,12 +212,6 @@ __device__ __forceinline__ void hopping(const Geom &g, const void *in, const voi
     }
 }
 
-// Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks
-// the site tiles bx, bx + gridDim.x, ... (grid-stride, so the grid can be sized to
-// the machine and reductions have one partial per resident block); thread (x, y)
-// handles right-hand side by * rhs_tile + y.  Ep::site consumes the hopping sum of
-// one site; Ep::finish runs once per thread after the loop (block and grid
-// reductions, solver scalars).
 // ---------------------------------------------------------------- checkerboard
 // Even-odd fields hold one parity of the lattice: the site with full index n
 // (parity (x+y+z+t) mod 2) sits at n / 2 of its parity's arrays (all extents
@@ -319,24 +313,16 @@ template <class R> __device__ __forceinline__ C<R> times_f(C<R> d, bool im, bool
     return cxsign(t, neg);
 }
 
-// the 3 colour components of spin sp of site s (F64 and DF32 layouts: one array per component)
+// the 3 colour components of spin sp of site s (FP64 layout: one array per component;
+// DF32 has its packed form, load_spin_cd)
 template <int P, bool NC, class R>
 __device__ __forceinline__ void load_spin(const void *base, int Vs, int s, int sp, C<R> (&v)[3]) {
-    static_assert(P == F64 || P == DF32, "per-component spinor arrays");
-    if constexpr (P == F64) {
-        const double2 *q = reinterpret_cast<const double2 *>(base) + (size_t)(3 * sp) * Vs + s;
+    static_assert(P == F64, "per-component FP64 spinor arrays");
+    const double2 *q = reinterpret_cast<const double2 *>(base) + (size_t)(3 * sp) * Vs + s;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double2 t = ldx<NC>(q + (size_t)c * Vs);
-            v[c] = C<R>{t.x, t.y};
-        }
-    } else {
-        const float4 *q = reinterpret_cast<const float4 *>(base) + (size_t)(3 * sp) * Vs + s;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float4 t = ldx<NC>(q + (size_t)c * Vs);
-            v[c] = C<R>{df(t.x, t.z), df(t.y, t.w)};
-        }
+    for (int c = 0; c < 3; ++c) {
+        const double2 t = ldx<NC>(q + (size_t)c * Vs);
+        v[c] = C<R>{t.x, t.y};
     }
 }
 
@@ -596,9 +582,7 @@ __device__ __forceinline__ void hopping_half(const Geom &g, const void *in, cons
             f2_unpack(a9[k].lo, rl, il);
             acc[k] = C<R>{df(rh, rl), df(ih, il)};
         }
-        return;
-    }
-    if constexpr (EO) {
+    } else if constexpr (EO) {
         int x, y, z, t;
         const int n = eo_full_index(g, s, x, y, z, t);
         const char *gp = reinterpret_cast<const char *>(gauge) + (size_t)(4 * g.eo_parity) * gdir_bytes;
@@ -704,6 +688,13 @@ __device__ __forceinline__ void store_part(const Pt &pt, void *base, int Vs, int
 // registers); FP64 and DF32 are arithmetic-bound and keep the compiler's choice.
 template <int P> constexpr int dslash_min_blocks() { return (P == F32 || P == F16) ? 3 : 0; }
 
+// Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks
+// the site tiles bx, bx + gridDim.x, ... (grid-stride, so a grid smaller than the
+// lattice bounds the number of reduction partials); thread (x, y) handles right-hand
+// side by * rhs_tile + y, and one site (FP32, FP16) or half a site (FP64, DF32: tiles
+// of site_tile / 2 sites).  Ep::site consumes the hopping sum of one site (or of the
+// lane's two spins); Ep::finish runs once per thread after the loop (block and grid
+// reductions, solver scalars).
 template <int P, int RECON, bool DAG, class Ep, bool EO = false>
 __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(DslashArgs a) {
     using R = typename Real<P>::T;
