@@ -90,27 +90,6 @@ __device__ __forceinline__ void accumulate(C<R> (&acc)[12], const C<R> (&w)[6]) 
 template <int P> struct HasScale { static constexpr bool value = false; };
 template <> struct HasScale<F16> { static constexpr bool value = true; };
 
-// w = scale * U h (forward) or scale * U^dag h (backward), two colour vectors
-template <bool ADJ, class R>
-__device__ __forceinline__ void su3_mult_scaled(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], R scale) {
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            C<R> s;
-            if (!ADJ) {
-                s = cmul(u[3 * a + 0], h[3 * sp + 0]);
-                s = cmac(s, u[3 * a + 1], h[3 * sp + 1]);
-                s = cmac(s, u[3 * a + 2], h[3 * sp + 2]);
-            } else {
-                s = cmulc(u[0 + a], h[3 * sp + 0]);
-                s = cmacc(s, u[3 + a], h[3 * sp + 1]);
-                s = cmacc(s, u[6 + a], h[3 * sp + 2]);
-            }
-            w[3 * sp + a] = cscale(scale, s);
-        }
-}
-
 // w = U h (forward) or U^dag h (backward), two colour vectors; optional sign flip
 template <bool ADJ, class R>
 __device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], bool flip) {
@@ -158,32 +137,145 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
     }
 }
 
-// FP16: project the raw half values, then apply the site scale and the boundary
-// sign once, to U h (12 multiplies instead of 24 per neighbour).
+// ---------------------------------------------------------------- FP16 on half operands
+// FP16 spinors (scaled to the site maximum) and links stay in half precision up to
+// the SU(3) product: the projection adds the two half values of each pair (HADD2,
+// one rounding to half, the size of the storage rounding), and U h is formed by FMAs
+// with half multiplicands and FP32 accumulators (fma.rn.f32.f16 of sm_100+: a product
+// of two halves is exact in FP32).  No half value is converted on the way.  The site
+// scale and the boundary sign enter once, in the FP32 multiply-adds that accumulate
+// U h.  (GB300 probe: 33 T such FMAs/s against 20 T/s for two conversions and an FFMA.)
+typedef uint32_t h2;  // a half2, real part in the low half, as its bits
+
+__device__ __forceinline__ h2 h2_add(h2 a, h2 b) {
+    const __half2 r = __hadd2(*reinterpret_cast<const __half2 *>(&a), *reinterpret_cast<const __half2 *>(&b));
+    return *reinterpret_cast<const h2 *>(&r);
+}
+__device__ __forceinline__ h2 h2_sub(h2 a, h2 b) {
+    const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&a), *reinterpret_cast<const __half2 *>(&b));
+    return *reinterpret_cast<const h2 *>(&r);
+}
+__device__ __forceinline__ h2 h2_neg(h2 a) { return a ^ 0x80008000u; }
+__device__ __forceinline__ h2 h2_muli(h2 a) { return ((a >> 16) | (a << 16)) ^ 0x00008000u; }  // i (x + iy) = -y + ix
+
+// s + u h: re += ur hr - ui hi, im += ur hi + ui hr (hn: h with its imaginary half negated)
+__device__ __forceinline__ void cmac_h(C<float> &s, h2 u, h2 h, h2 hn) {
+    asm("{\n\t.reg .f16 ur, ui, hr, hi, nr, ni;\n\t"
+        "mov.b32 {ur, ui}, %2;\n\tmov.b32 {hr, hi}, %3;\n\tmov.b32 {nr, ni}, %4;\n\t"
+        "fma.rn.f32.f16 %0, ur, hr, %0;\n\tfma.rn.f32.f16 %0, ui, ni, %0;\n\t"
+        "fma.rn.f32.f16 %1, ur, hi, %1;\n\tfma.rn.f32.f16 %1, ui, hr, %1;\n\t}"
+        : "+f"(s.re), "+f"(s.im) : "r"(u), "r"(h), "r"(hn));
+}
+// s + conj(u) h: re += ur hr + ui hi, im += ur hi - ui hr (hn: h with its real half negated)
+__device__ __forceinline__ void cmacc_h(C<float> &s, h2 u, h2 h, h2 hn) {
+    asm("{\n\t.reg .f16 ur, ui, hr, hi, nr, ni;\n\t"
+        "mov.b32 {ur, ui}, %2;\n\tmov.b32 {hr, hi}, %3;\n\tmov.b32 {nr, ni}, %4;\n\t"
+        "fma.rn.f32.f16 %0, ur, hr, %0;\n\tfma.rn.f32.f16 %0, ui, hi, %0;\n\t"
+        "fma.rn.f32.f16 %1, ur, hi, %1;\n\tfma.rn.f32.f16 %1, ui, nr, %1;\n\t}"
+        : "+f"(s.re), "+f"(s.im) : "r"(u), "r"(h), "r"(hn));
+}
+
+// the 12 raw half2 components of site s and its scale
+template <bool NC>
+__device__ __forceinline__ float load_raw_h2(const void *base, int Vs, int s, h2 (&v)[12]) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(base) + s;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const uint4 t = ldx<NC>(p + (size_t)j * Vs);
+        v[4 * j + 0] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+    return ldx<NC>(SpinorIO<F16>::norms(base, Vs) + s);
+}
+
+// the 9 link entries as half2 (recon-12/8 rows are rebuilt in FP32 and rounded to half)
+template <int RECON>
+__device__ __forceinline__ void load_link_h2(const char *gdir, int Vs, int s, h2 (&u)[9]) {
+    if constexpr (RECON == 18) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(gdir) + s;
+        const uint4 a = __ldg(p), b = __ldg(p + Vs);
+        u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+        u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+        u[8] = __ldg(reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint4 *>(gdir) + (size_t)2 * Vs) + s);
+    } else {
+        C<float> w[9];
+        LinkIO<F16, RECON>::load(gdir, Vs, s, w);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) u[e] = f2h(w[e].re, w[e].im);
+    }
+}
+
+// h = psi_up + S A_mu psi_dn on half2 values (the half-precision projection)
+template <int MU, int S>
+__device__ __forceinline__ void project_h2(const h2 (&p)[12], h2 (&h)[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const h2 d2 = p[6 + c], d3 = p[9 + c];
+        h2 a0, a1;
+        if (MU == 0) { a0 = h2_muli(d3); a1 = h2_muli(d2); }
+        else if (MU == 1) { a0 = h2_neg(d3); a1 = d2; }
+        else if (MU == 2) { a0 = h2_muli(d2); a1 = h2_neg(h2_muli(d3)); }
+        else { a0 = d2; a1 = d3; }
+        h[c] = S > 0 ? h2_add(p[c], a0) : h2_sub(p[c], a0);
+        h[3 + c] = S > 0 ? h2_add(p[3 + c], a1) : h2_sub(p[3 + c], a1);
+    }
+}
+
+// acc_up += sc w, acc_dn += S sc A_mu^dag w (FP32 multiply-adds; sc: scale and sign)
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_scaled(C<float> (&acc)[12], const C<float> (&w)[6], float sc) {
+    const float ss = S > 0 ? sc : -sc;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const C<float> w0 = w[c], w1 = w[3 + c];
+        acc[c] = C<float>{fmaf(sc, w0.re, acc[c].re), fmaf(sc, w0.im, acc[c].im)};
+        acc[3 + c] = C<float>{fmaf(sc, w1.re, acc[3 + c].re), fmaf(sc, w1.im, acc[3 + c].im)};
+        C<float> b0, b1;  // A^dag (w0, w1)
+        if (MU == 0) { b0 = cneg(cmuli(w1)); b1 = cneg(cmuli(w0)); }
+        else if (MU == 1) { b0 = w1; b1 = cneg(w0); }
+        else if (MU == 2) { b0 = cneg(cmuli(w0)); b1 = cmuli(w1); }
+        else { b0 = w0; b1 = w1; }
+        acc[6 + c] = C<float>{fmaf(ss, b0.re, acc[6 + c].re), fmaf(ss, b0.im, acc[6 + c].im)};
+        acc[9 + c] = C<float>{fmaf(ss, b1.re, acc[9 + c].re), fmaf(ss, b1.im, acc[9 + c].im)};
+    }
+}
+
+// one FP16 hop: neighbour spinor at index sn, link at index sl of gdir (its adjoint for
+// ADJ), projector sign S, boundary sign flip
+template <int RECON, bool ADJ, int MU, int S, bool NC>
+__device__ __forceinline__ void hop_f16(const void *in, int Vs, int sn, const char *gdir, int sl, bool flip,
+                                        C<float> (&acc)[12]) {
+    h2 p[12], h[6], hn[6], u[9];
+    const float scale = load_raw_h2<NC>(in, Vs, sn, p);
+    project_h2<MU, S>(p, h);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hn[k] = h[k] ^ (ADJ ? 0x00008000u : 0x80000000u);
+    load_link_h2<RECON>(gdir, Vs, sl, u);
+    C<float> w[6];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C<float> t{0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (!ADJ) cmac_h(t, u[3 * a + b], h[3 * sp + b], hn[3 * sp + b]);
+                else cmacc_h(t, u[3 * b + a], h[3 * sp + b], hn[3 * sp + b]);
+            }
+            w[3 * sp + a] = t;
+        }
+    accumulate_scaled<MU, S>(acc, w, flip ? -scale : scale);
+}
+
 template <int P, int RECON, bool DAG, int MU, bool NC = true>
 __device__ __forceinline__ void hop_dir_scaled(const Geom &g, const void *in, const char *gdir, int s, int c,
                                                C<typename Real<P>::T> (&acc)[12]) {
-    using R = typename Real<P>::T;
+    static_assert(P == F16, "FP16 hop");
     constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
-    {
-        const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
-        C<R> p[12], h[6], w[6], u[9];
-        const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sf, p);
-        project<MU, SF>(p, h);
-        LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
-        su3_mult_scaled<false>(u, h, w, (MU == 3 && g.antiperiodic && c == L - 1) ? -scale : scale);
-        accumulate<MU, SF>(acc, w);
-    }
-    {
-        const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
-        C<R> p[12], h[6], w[6], u[9];
-        const R scale = SpinorIO<P>::template load_raw<NC>(in, g.Vs, sb, p);
-        project<MU, -SF>(p, h);
-        LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
-        su3_mult_scaled<true>(u, h, w, (MU == 3 && g.antiperiodic && c == 0) ? -scale : scale);
-        accumulate<MU, -SF>(acc, w);
-    }
+    const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
+    hop_f16<RECON, false, MU, SF, NC>(in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1, acc);
+    const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
+    hop_f16<RECON, true, MU, -SF, NC>(in, g.Vs, sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, acc);
 }
 
 // acc = sum over the 8 hops (the bracket of Eq. (1)) at site s of field `in`.
@@ -237,23 +329,30 @@ __device__ __forceinline__ void hop_dir_eo(const Geom &g, const void *in, const 
     using R = typename Real<P>::T;
     constexpr int SF = DAG ? +1 : -1;
     const int L = g.L[MU], st = g.stride[MU];
-    {
+    if constexpr (P == F16) {
         const int nf = WD_IDX(g, (c == L - 1) ? n - (L - 1) * st : n + st, 2 * g.V, 3);
-        C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, p);
-        project<MU, SF>(p, h);
-        LinkIO<P, RECON>::load(gp, g.Vs, k, u);
-        su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
-        accumulate<MU, SF>(acc, w);
-    }
-    {
+        hop_f16<RECON, false, MU, SF, NC>(in, g.Vs, nf >> 1, gp, k, MU == 3 && g.antiperiodic && c == L - 1, acc);
         const int nb = WD_IDX(g, (c == 0) ? n + (L - 1) * st : n - st, 2 * g.V, 4);
-        C<R> p[12], h[6], w[6], u[9];
-        SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, p);
-        project<MU, -SF>(p, h);
-        LinkIO<P, RECON>::load(gq, g.Vs, nb >> 1, u);
-        su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
-        accumulate<MU, -SF>(acc, w);
+        hop_f16<RECON, true, MU, -SF, NC>(in, g.Vs, nb >> 1, gq, nb >> 1, MU == 3 && g.antiperiodic && c == 0, acc);
+    } else {
+        {
+            const int nf = WD_IDX(g, (c == L - 1) ? n - (L - 1) * st : n + st, 2 * g.V, 3);
+            C<R> p[12], h[6], w[6], u[9];
+            SpinorIO<P>::template load<NC>(in, g.Vs, nf >> 1, p);
+            project<MU, SF>(p, h);
+            LinkIO<P, RECON>::load(gp, g.Vs, k, u);
+            su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
+            accumulate<MU, SF>(acc, w);
+        }
+        {
+            const int nb = WD_IDX(g, (c == 0) ? n + (L - 1) * st : n - st, 2 * g.V, 4);
+            C<R> p[12], h[6], w[6], u[9];
+            SpinorIO<P>::template load<NC>(in, g.Vs, nb >> 1, p);
+            project<MU, -SF>(p, h);
+            LinkIO<P, RECON>::load(gq, g.Vs, nb >> 1, u);
+            su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+            accumulate<MU, -SF>(acc, w);
+        }
     }
 }
 

@@ -197,22 +197,6 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
 template <> struct SpinorIO<F16> {
     using R = float;
     static constexpr bool kScaled = true;
-    // raw half values (|v| <= 1) and the site scale, for callers that apply the
-    // scale once to a derived quantity instead of to all 24 reals
-    template <bool NC = true>
-    static __device__ __forceinline__ float load_raw(const void *base, int Vs, int s, C<R> (&v)[12]) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(base) + s;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            uint4 t = ldx<NC>(p + (size_t)j * Vs);
-            float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
-            v[4 * j + 0] = C<R>{a.x, a.y};
-            v[4 * j + 1] = C<R>{b.x, b.y};
-            v[4 * j + 2] = C<R>{c.x, c.y};
-            v[4 * j + 3] = C<R>{d.x, d.y};
-        }
-        return ldx<NC>(norms(base, Vs) + s);
-    }
     static __device__ __forceinline__ const float *norms(const void *base, int Vs) {
         return reinterpret_cast<const float *>(reinterpret_cast<const char *>(base) + (size_t)3 * Vs * 16);
     }
