@@ -74,7 +74,9 @@ typedef enum wd_status {
 /* Storage and arithmetic precision of a field and of the operator applied to it.
  *   WD_F64   IEEE double.
  *   WD_F32   IEEE single.
- *   WD_F16   half-precision storage with a per-site FP32 scale, FP32 arithmetic.
+ *   WD_F16   half-precision storage with a per-site FP32 scale, FP32 accumulation:
+ *            the spin projection adds half values in half precision and the SU(3)
+ *            products multiply half values into FP32 sums (exact products).
  *   WD_DF32  double-FP32: every real is the unevaluated sum of two floats (48-bit
  *            significand), stored in the same 16 bytes per complex number as
  *            WD_F64 and computed on the FP32 pipes with error-free transformations
@@ -179,7 +181,7 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *   max_iter   iteration limit
  *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16 / WD_DF32: mixed precision --
  *              the Dslash and the inner iteration in FP32 (or FP16 storage with FP32
- *              arithmetic, or double-FP32), with FP64 reliable updates
+ *              accumulation, or double-FP32), with FP64 reliable updates
  *              r = D^dag(b - D x) and the solution accumulated in FP64
  *   delta      reliable-update trigger: an update runs when the iterated residual
  *              drops below delta times its maximum since the last update (0 = the
@@ -230,8 +232,10 @@ typedef struct wd_cg_result {
 /* Solve D x = b for nrhs right-hand sides by CG on D^dag D x = D^dag b, entirely on
  * the device (a CUDA graph with a device-side loop).  b, x: WD_F64 fields of
  * params->nrhs right-hand sides; x holds the initial guess on entry (zeros for the
- * default start; section 2.2, psi <- psi_0) and the solution on exit.  result points
- * to params->nrhs results.  Returns WD_OK when every right-hand side converged. */
+ * default start; section 2.2, psi <- psi_0) and the solution on exit; for an all-zero
+ * guess the setup skips its two operator applications on x (a device-side test).
+ * result points to params->nrhs results.  Returns WD_OK when every right-hand side
+ * converged. */
 wd_status wd_cg_solve(wd_ctx *ctx, double kappa, const void *b, void *x, const wd_cg_params *params,
                       wd_cg_result *result);
 
@@ -245,7 +249,8 @@ wd_status wd_cg_solve_canonical(wd_ctx *ctx, double kappa, const double *b_canon
  * kappa, in one persistent cooperative kernel launch, with mixed-precision
  * (inner_prec) CG and FP64 reliable updates.  All contexts must live on the same
  * device; the work runs on ctxs[0]'s stream.  b[i], x[i]: WD_F64 fields of ctxs[i]
- * (one right-hand side); result[i] receives lattice i's result.  Grid-wide waits
+ * (one right-hand side); result[i] receives lattice i's result.  Every context needs
+ * the same link compression for FP64 and the inner precision.  Grid-wide waits
  * inside the kernel are bounded; when one runs out, every result gets
  * WD_ERR_TIMEOUT and the kernel returns. */
 wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const void *const *b, void *const *x,
