@@ -551,6 +551,8 @@ def compare(args):
         for dims, seed in zip(shapes, seeds):
             lat = wd.Lattice(dims)
             lat.set_gauge(gen.haar_links(dims, seed), recon=args.recon)
+            if args.recon_inner:
+                lat.set_link_compression(wd.WD_F32, args.recon_inner)
             lats.append(lat)
             bs.append(lat.pack(gen.gaussian_source(dims, seed)))
             xs.append(lat.new_field())
@@ -575,7 +577,8 @@ def compare(args):
         ms_s, res_s = _timed_solves(torch, one_by_one, reps)
         err = max(oracle.rel_err(a, l.unpack(y)) for a, l, y in zip(xb, lats, ys))
         line["compare"] = {
-            "lattices": 64, "total_sites": V, "shapes": sorted(set("x".join(map(str, d)) for d in shapes)),
+            "lattices": 64, "total_sites": V, "recon": args.recon, "recon_inner": args.recon_inner or args.recon,
+            "shapes": sorted(set("x".join(map(str, d)) for d in shapes)),
             "batched_mixed_f32": {"ms": round(ms_b, 3), "solves_per_s": round(64e3 / ms_b, 1),
                                   "per_solve_latency_ms": round(ms_b, 3), "status": st_b,
                                   "max_true_rel_resid": max(r["true_rel_resid"] for r in res_b),

@@ -123,9 +123,9 @@ wd_status wd_debug_word(wd_ctx *ctx, unsigned *word, int *is_debug);
  * arithmetic there, while the FP32/FP16 operators are bound by memory and gain from
  * them; a mixed-precision solve can keep FP64 links whole (18) and compress the inner
  * precision's (12).  Applies until the next wd_set_gauge, which resets every precision
- * to its recon.  The solvers accept any compression for the inner precision when the
- * FP64 links are whole, and otherwise the same compression for both; the batched
- * solver needs the same compression for both.  Errors: WD_ERR_ARG (bad precision or
+ * to its recon.  The solvers (wd_cg_solve* and wd_cg_solve_batched) accept any
+ * compression for the inner precision when the FP64 links are whole, and otherwise
+ * the same compression for both.  Errors: WD_ERR_ARG (bad precision or
  * recon, links unsuited to recon 8), WD_ERR_STATE (no gauge field yet). */
 wd_status wd_set_link_compression(wd_ctx *ctx, wd_prec prec, int recon);
 
@@ -250,7 +250,8 @@ wd_status wd_cg_solve_canonical(wd_ctx *ctx, double kappa, const double *b_canon
  * (inner_prec) CG and FP64 reliable updates.  All contexts must live on the same
  * device; the work runs on ctxs[0]'s stream.  b[i], x[i]: WD_F64 fields of ctxs[i]
  * (one right-hand side); result[i] receives lattice i's result.  Every context needs
- * the same link compression for FP64 and the inner precision.  Grid-wide waits
+ * the same pair of link compressions (FP64, inner precision), a pair that
+ * wd_set_link_compression's rule allows.  Grid-wide waits
  * inside the kernel are bounded; when one runs out, every result gets
  * WD_ERR_TIMEOUT and the kernel returns. */
 wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const void *const *b, void *const *x,

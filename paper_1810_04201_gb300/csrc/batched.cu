@@ -133,7 +133,7 @@ __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
     }
 }
 
-template <int SP, int RECON>
+template <int SP, int RECON, int RIN>
 __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
     auto all = [](const Scalars &) { return 1; };
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
             double v[1] = {0.0};
             if (valid) {
                 C<RS> acc[12], p[12];
-                hopping<SP, RECON, false, false>(L.g, L.ps, L.gs, L.gdirs, s, acc);
+                hopping<SP, RIN, false, false>(L.g, L.ps, L.gs, L.gdirs, s, acc);
                 SpinorIO<SP>::template load<false>(L.ps, L.g.Vs, s, p);
                 xpay_site(p, acc, RS(L.kappa));
                 v[0] = norm2_of(p);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
             if (valid) {
                 const RS alpha = RS(a.sc[l].alpha);
                 C<RS> acc[12], q[12], w[12];
-                hopping<SP, RECON, true, false>(L.g, L.ts, L.gs, L.gdirs, s, acc);
+                hopping<SP, RIN, true, false>(L.g, L.ts, L.gs, L.gdirs, s, acc);
                 SpinorIO<SP>::template load<false>(L.ts, L.g.Vs, s, q);
                 xpay_site(q, acc, RS(L.kappa));
                 SpinorIO<SP>::template load<false>(L.rs, L.g.Vs, s, w);
@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
 
 // One persistent cooperative launch, captured once into a CUDA graph per argument
 // set (the arguments are pointers into context workspace, stable across calls).
-template <int SP, int RECON>
+template <int SP, int RECON, int RIN>
 static cudaError_t build_batched(BatchArgs &a, cudaGraphExec_t *exec) {
-    auto k = k_batched_cg<SP, RECON>;
+    auto k = k_batched_cg<SP, RECON, RIN>;
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTile, 0);
     if (e != cudaSuccess) return e;
@@ -449,9 +449,8 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
         if (!c || !b[i] || !x[i] || !std::isfinite(kappas[i]))
             return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: null context, field or bad kappa");
         if (c->device != c0->device) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: contexts on different devices");
-        if (link_recon(c, F64) != link_recon(c0, F64) || link_recon(c, sp) != link_recon(c, F64))
-            return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: every context needs one link compression for FP64 "
-                                        "and the inner precision");
+        if (link_recon(c, F64) != link_recon(c0, F64) || link_recon(c, sp) != link_recon(c0, sp))
+            return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: every context needs the same link compressions");
         wd_status s;
         const void *g64, *gs;
         if ((s = gauge_get(c, F64, &g64)) != WD_OK) return fail(c0, s, c->last_error);
@@ -526,17 +525,21 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     // about one second at GB300 clocks; a tenth of that for the stalled-wait test
     a.spin_limit = a.stall_test ? 200000000ll : 2000000000ll;
 
+    const int r64 = link_recon(c0, F64), rin = link_recon(c0, sp);
+    if (rin != r64 && r64 != 18)
+        return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: with compressed FP64 links the inner precision needs the "
+                                    "same compression");
     char key[160];
-    snprintf(key, sizeof key, "batch|%d|%d|%d|%d|%d|%d|%p|%p", (int)sp, link_recon(c0, F64), n, ntiles, prm->max_iter,
+    snprintf(key, sizeof key, "batch|%d|%d,%d|%d|%d|%d|%d|%p|%p", (int)sp, r64, rin, n, ntiles, prm->max_iter,
              a.stall_test, d_part, d_lat);
     cudaGraphExec_t exec;
     auto it = c0->graphs.find(key);
     if (it != c0->graphs.end()) {
         exec = (cudaGraphExec_t)it->second;
     } else {
-        const cudaError_t e = with_recon(link_recon(c0, F64), [&](auto rc) {
-            constexpr int R = decltype(rc)::value;
-            return sp == F32 ? build_batched<F32, R>(a, &exec) : build_batched<F16, R>(a, &exec);
+        const cudaError_t e = with_recon_pair(r64, rin, [&](auto ra, auto rb) {
+            constexpr int R = decltype(ra)::value, RI = decltype(rb)::value;
+            return sp == F32 ? build_batched<F32, R, RI>(a, &exec) : build_batched<F16, R, RI>(a, &exec);
         });
         if (e != cudaSuccess) return cuda_fail(c0, e, "building the batched persistent CG graph");
         c0->graphs[key] = exec;

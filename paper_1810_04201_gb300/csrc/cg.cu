@@ -25,13 +25,6 @@ cudaError_t build_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const vo
 template <int RECON, int RIN>
 void record_for(wd_ctx *c, const SolverPlan &pl, const Fields &f, const void *g64, const void *gin, Plan &plan);
 
-// Calls fn(integral_constant<R64>, integral_constant<RIN>) for the built pairs.
-template <class F> static decltype(auto) with_recon_pair(int r64, int rin, F &&fn) {
-    using std::integral_constant;
-    if (r64 == 18 && rin == 12) return fn(integral_constant<int, 18>{}, integral_constant<int, 12>{});
-    if (r64 == 18 && rin == 8) return fn(integral_constant<int, 18>{}, integral_constant<int, 8>{});
-    return with_recon(r64, [&](auto rc) { return fn(rc, rc); });
-}
 
 // The same plan launched kernel by kernel from the host; the active flags are read
 // back every `chunk` iterations.  Loop kernels of converged rows return at once,

@@ -57,6 +57,16 @@ template <class F> decltype(auto) with_recon(int recon, F &&f) {
 // WD_ERR_ARG unless every link suits the 8-real parametrisation (see wd_set_gauge)
 wd_status check_recon8(wd_ctx *c, const char *who);
 
+// Calls f(integral_constant<R64>, integral_constant<RIN>) for the pairs of link
+// compressions (FP64, inner precision) the solvers are built for: equal ones, and
+// whole FP64 links beside recon-12 or recon-8 inner links.
+template <class F> decltype(auto) with_recon_pair(int r64, int rin, F &&f) {
+    using std::integral_constant;
+    if (r64 == 18 && rin == 12) return f(integral_constant<int, 18>{}, integral_constant<int, 12>{});
+    if (r64 == 18 && rin == 8) return f(integral_constant<int, 18>{}, integral_constant<int, 8>{});
+    return with_recon(r64, [&](auto rc) { return f(rc, rc); });
+}
+
 // workspace: named device buffer of at least `bytes` (kept across calls)
 wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out);
 // device gauge field of precision p at the context's recon (created on first use)

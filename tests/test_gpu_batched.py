@@ -77,3 +77,33 @@ def test_batched_argument_errors(wd):
     lats[1].set_gauge(gen.haar_links(lats[1].dims, 3), recon=12)
     res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
     assert st == 1
+
+
+@pytest.mark.parametrize("inner,rin", [(1, 12), (1, 8), (2, 12)])
+def test_batched_whole_fp64_links_compressed_inner(wd, inner, rin):
+    """Whole FP64 links beside compressed inner links in the persistent kernel: same solutions."""
+    lats, kappas, bs, xs, inputs = make_batch(wd)
+    for lat in lats:
+        lat.set_link_compression(inner, rin)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=inner)
+    assert st == 0, res
+    for i, (lat, (U, b)) in enumerate(zip(lats, inputs)):
+        assert res[i]["status"] == 0 and res[i]["true_rel_resid"] <= 1e-10
+        x_ref, _ = oracle.cgnr(U, b, kappas[i], lat.dims, tol=1e-13)
+        assert oracle.rel_err(lat.unpack(xs[i]), x_ref) < 1e-9, i
+
+
+def test_batched_link_compression_rules(wd):
+    """Compressed FP64 links need the same inner compression; every context the same pair."""
+    lats, kappas, bs, xs, _ = make_batch(wd, recon=12)
+    for lat in lats:
+        lat.set_link_compression(1, 18)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 1
+    lats, kappas, bs, xs, _ = make_batch(wd)
+    lats[2].set_link_compression(1, 12)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 1
+    lats[2].set_link_compression(1, 18)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 0
