@@ -10,6 +10,10 @@
 // lattice's last tile sums them in tile order (deterministic) and advances that
 // lattice's scalar recursion, so every phase needs exactly one barrier.
 // Converged lattices drop out of the list; the kernel ends when none is left.
+// The FP64 phases (setup, reliable updates, final check) run two lanes per site
+// with paired hops, like the FP64 Dslash kernel; a zero start vector skips the
+// setup's D x0 and D^dag D x0; a reliable update that stops a lattice doubles as
+// its final check.
 //
 // Grid barriers spin on a generation counter with a cycle limit: when it runs
 // out the waiting block raises an error flag, every block leaves the kernel at
@@ -27,6 +31,8 @@ using namespace wd;
 namespace wd {
 
 constexpr int kTile = 128;
+constexpr int kHalfTile = kTile / 2;  // sites of one pass of the two-lane FP64 phases
+constexpr int kPart = 4;              // partial sums per tile
 
 struct LatDesc {
     Geom g;
@@ -46,6 +52,7 @@ struct BatchArgs {
     int ntiles, nlat, max_iter;
     unsigned *bar_count, *bar_gen;
     int *flags;          // [0] error, [1] any reliable update pending, [2] iterations run, [3] never set
+    int *lstate;         // per lattice: [0] start vector nonzero, [1] the last reliable update was the final check
     long long spin_limit;
     int stall_test;      // block 0 first waits on flags[3], which nothing sets
 };
@@ -91,7 +98,7 @@ __device__ void tile_reduce(const BatchArgs &a, const LatDesc &L, int g, int l, 
     block_reduce_rows<NV>(v, red);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) a.tpart[(size_t)g * 2 + k] = v[k];
+        for (int k = 0; k < NV; ++k) a.tpart[(size_t)g * kPart + k] = v[k];
         __threadfence();
         last = atomicAdd(a.lcount + l, 1u) == (unsigned)L.ntiles - 1;
     }
@@ -103,7 +110,7 @@ __device__ void tile_reduce(const BatchArgs &a, const LatDesc &L, int g, int l, 
     for (int k = 0; k < NV; ++k) s[k] = 0.0;
     for (int i = threadIdx.x; i < L.ntiles; i += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] += __ldcg(a.tpart + (size_t)(L.tile0 + i) * 2 + k);
+        for (int k = 0; k < NV; ++k) s[k] += __ldcg(a.tpart + (size_t)(L.tile0 + i) * kPart + k);
     __syncthreads();
     block_reduce_rows<NV>(s, red);
     if (threadIdx.x == 0) {
@@ -113,7 +120,8 @@ __device__ void tile_reduce(const BatchArgs &a, const LatDesc &L, int g, int l, 
     __syncthreads();
 }
 
-// One phase: walk the tiles of the lattices selected by `want(sc)`.
+// One phase: walk the tiles of the lattices selected by `want(sc, lattice)`, one
+// thread per site.
 template <class W, class F>
 __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
     __shared__ LatDesc L;
@@ -121,7 +129,7 @@ __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
     for (int g = blockIdx.x; g < a.ntiles; g += gridDim.x) {
         const int l = a.tile_lat[g];
         if (threadIdx.x == 0) {
-            run = want(a.sc[l]);
+            run = want(a.sc[l], l);
             if (run) L = a.lat[l];
         }
         __syncthreads();
@@ -133,12 +141,51 @@ __device__ void for_tiles(const BatchArgs &a, W &&want, F &&body) {
     }
 }
 
+// The FP64 phases run two lanes per site like the FP64 Dslash kernel: lanes l and
+// l ^ 16 of a warp share a site (lane half hh), so a tile takes two passes of
+// kHalfTile sites; `body(L, g, l, sl, hh)` gets the lane's site offset sl within a pass.
+template <class W, class F>
+__device__ void for_tiles_half(const BatchArgs &a, W &&want, F &&body) {
+    __shared__ LatDesc L;
+    __shared__ int run;
+    const int hh = (threadIdx.x >> 4) & 1;
+    const int sl = ((threadIdx.x >> 5) << 4) | (threadIdx.x & 15);
+    for (int g = blockIdx.x; g < a.ntiles; g += gridDim.x) {
+        const int l = a.tile_lat[g];
+        if (threadIdx.x == 0) {
+            run = want(a.sc[l], l);
+            if (run) L = a.lat[l];
+        }
+        __syncthreads();
+        if (run) body(L, g, l, sl, hh);
+        __syncthreads();
+    }
+}
+
+// The hopping sum of lane half hh at site s (zero where `on` is false), exchanged
+// with the partner lane: the lane's two spins (SiteHalf).  Every lane of the warp
+// calls it.  Plain loads: the fields change between the phases of one launch.
+template <int RECON, bool DAG>
+__device__ __forceinline__ void hop64_half(const LatDesc &L, const void *in, int s, int hh, bool on,
+                                           C<double> (&own)[6]) {
+    C<double> acc[9];
+    if (on) hopping_half<F64, RECON, DAG, false, false>(L.g, in, L.g64, L.gdir64, s, hh, acc);
+    else
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = C<double>{0.0, 0.0};
+    exchange_halves(acc);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) own[k] = acc[k];
+}
+
 template <int SP, int RECON, int RIN>
-__global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
+__global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
-    auto all = [](const Scalars &) { return 1; };
-    auto active = [](const Scalars &c) { return c.active; };
-    auto updating = [](const Scalars &c) { return c.active && c.do_update; };
+    auto all = [](const Scalars &, int) { return 1; };
+    auto active = [](const Scalars &c, int) { return c.active; };
+    auto updating = [](const Scalars &c, int) { return c.active && c.do_update; };
+    auto x0_nonzero = [&](const Scalars &, int l) { return a.lstate[2 * l]; };
+    auto unchecked = [&](const Scalars &, int l) { return 1 - a.lstate[2 * l + 1]; };
 
     if (a.stall_test && blockIdx.x == 0 && threadIdx.x == 0) {
         // a wait that runs out: nothing ever sets flags[3]
@@ -148,61 +195,101 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
         if (*never == 0) atomicExch(a.flags, 1);
     }
 
-    // ---- setup (FP64): db = D^dag b, |db|^2, |b|^2 ; t = D x0
-    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
-        double v[2] = {0.0, 0.0};
-        if (valid) {
-            C<double> acc[12], p[12];
-            hopping<F64, RECON, true, false>(L.g, L.b, L.g64, L.gdir64, s, acc);
-            SpinorIO<F64>::template load<false>(L.b, L.g.Vs, s, p);
-            v[1] = norm2_of(p);
-            xpay_site(p, acc, L.kappa);
-            v[0] = norm2_of(p);
-            SpinorIO<F64>::store(L.db, L.g.Vs, s, p);
-            hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
-            SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
-            xpay_site(p, acc, L.kappa);
-            SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
+    // ---- setup (FP64, two lanes per site)
+    // S1: db = D^dag b ; |db|^2, |b|^2, |x0|^2 (a zero start vector skips S2 and the hop of S3)
+    for_tiles_half(a, all, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+        const SiteHalf pt{hh};
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+            const bool on = s < L.g.V;
+            C<double> acc[6], p[6];
+            hop64_half<RECON, true>(L, L.b, s, hh, on, acc);
+            if (on) {
+                load_part<F64, SiteHalf, false>(pt, L.b, L.g.Vs, s, p);
+                v[1] += norm2_of(p);
+                xpay_site(p, acc, L.kappa);
+                v[0] += norm2_of(p);
+                store_part<F64>(pt, L.db, L.g.Vs, s, p);
+                load_part<F64, SiteHalf, false>(pt, L.x, L.g.Vs, s, p);
+                v[2] += norm2_of(p);
+            }
         }
-        tile_reduce<2>(a, L, g, l, v, [&](int l2, const double *t) {
+        tile_reduce<3>(a, L, g, l, v, [&](int l2, const double *t) {
             Scalars &c = a.sc[l2];
             c.rhs2 = t[0];
             c.b2 = t[1];
             c.tol2 *= t[0];
+            a.lstate[2 * l2] = !(t[2] == 0.0);  // NaN counts as nonzero
         });
     });
     if (!grid_barrier(a)) return;
-    // r = db - D^dag t ; rs = ps = r (inner precision) ; xs = 0 ; rho = |r|^2
-    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
-        double v[1] = {0.0};
-        if (valid) {
-            C<double> acc[12], q[12], d[12];
-            hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
-            SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
-            xpay_site(q, acc, L.kappa);
-            SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
-            v[0] = norm2_of(d);
-            SpinorIO<F64>::store(L.r, L.g.Vs, s, d);
-            C<RS> w[12];
-            C<float> z[12];
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                w[c] = C<RS>{RS(d[c].re), RS(d[c].im)};
-                z[c] = C<float>{0.f, 0.f};
+    // S2: t = D x0
+    for_tiles_half(a, x0_nonzero, [&](const LatDesc &L, int g, int, int sl, int hh) {
+        const SiteHalf pt{hh};
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+            const bool on = s < L.g.V;
+            C<double> acc[6], p[6];
+            hop64_half<RECON, false>(L, L.x, s, hh, on, acc);
+            if (on) {
+                load_part<F64, SiteHalf, false>(pt, L.x, L.g.Vs, s, p);
+                xpay_site(p, acc, L.kappa);
+                store_part<F64>(pt, L.t, L.g.Vs, s, p);
             }
-            SpinorIO<SP>::store(L.rs, L.g.Vs, s, w);
-            SpinorIO<SP>::store(L.ps, L.g.Vs, s, w);
-            SpinorIO<F32>::store(L.xs, L.g.Vs, s, z);
+        }
+    });
+    if (!grid_barrier(a)) return;
+    // S3: r = db - D^dag t (r = db for x0 = 0) ; rho = |r|^2
+    for_tiles_half(a, all, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+        const SiteHalf pt{hh};
+        const bool nz = a.lstate[2 * l] != 0;
+        double v[1] = {0.0};
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+            const bool on = s < L.g.V;
+            C<double> acc[6], q[6], d[6];
+            hop64_half<RECON, true>(L, L.t, s, hh, on && nz, acc);
+            if (on) {
+                if (nz) {
+                    load_part<F64, SiteHalf, false>(pt, L.t, L.g.Vs, s, q);
+                    xpay_site(q, acc, L.kappa);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) q[k] = C<double>{0.0, 0.0};
+                }
+                load_part<F64, SiteHalf, false>(pt, L.db, L.g.Vs, s, d);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) d[k] = csub(d[k], q[k]);
+                v[0] += norm2_of(d);
+                store_part<F64>(pt, L.r, L.g.Vs, s, d);
+            }
         }
         tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
             Scalars &c = a.sc[l2];
             c.rho = t[0];
             c.rmax2 = t[0];
+            a.lstate[2 * l2 + 1] = 0;
             if (!isfinite(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; }
             else if (t[0] <= c.tol2) { c.status = WD_OK; c.active = 0; }
         });
+    });
+    if (!grid_barrier(a)) return;
+    // S4: rs = ps = r (inner precision) ; xs = 0
+    for_tiles(a, all, [&](const LatDesc &L, int, int, int s, bool valid) {
+        if (!valid) return;
+        C<double> d[12];
+        SpinorIO<F64>::template load<false>(L.r, L.g.Vs, s, d);
+        C<RS> w[12];
+        C<float> z[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            w[c] = C<RS>{RS(d[c].re), RS(d[c].im)};
+            z[c] = C<float>{0.f, 0.f};
+        }
+        SpinorIO<SP>::store(L.rs, L.g.Vs, s, w);
+        SpinorIO<SP>::store(L.ps, L.g.Vs, s, w);
+        SpinorIO<F32>::store(L.xs, L.g.Vs, s, z);
     });
     if (!grid_barrier(a)) return;
 
@@ -286,29 +373,46 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
                 SpinorIO<F32>::store(L.xs, L.g.Vs, s, xs);
             });
             if (!grid_barrier(a)) return;
-            // C2: t = D x (FP64)
-            for_tiles(a, updating, [&](const LatDesc &L, int, int, int s, bool valid) {
-                if (!valid) return;
-                C<double> acc[12], p[12];
-                hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
-                SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
-                xpay_site(p, acc, L.kappa);
-                SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
+            // C2: t = D x (FP64) ; |b - t|^2 (the final check's first norm, should x stay)
+            for_tiles_half(a, updating, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+                const SiteHalf pt{hh};
+                double v[1] = {0.0};
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+                    const bool on = s < L.g.V;
+                    C<double> acc[6], p[6], bb[6];
+                    hop64_half<RECON, false>(L, L.x, s, hh, on, acc);
+                    if (on) {
+                        load_part<F64, SiteHalf, false>(pt, L.x, L.g.Vs, s, p);
+                        xpay_site(p, acc, L.kappa);
+                        store_part<F64>(pt, L.t, L.g.Vs, s, p);
+                        load_part<F64, SiteHalf, false>(pt, L.b, L.g.Vs, s, bb);
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) bb[k] = csub(bb[k], p[k]);
+                        v[0] += norm2_of(bb);
+                    }
+                }
+                tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) { a.sc[l2].true_b2 = t[0]; });
             });
             if (!grid_barrier(a)) return;
             // C3: r = db - D^dag t ; rho = |r|^2 (the true residual of the normal equations)
-            for_tiles(a, updating, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+            for_tiles_half(a, updating, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+                const SiteHalf pt{hh};
                 double v[1] = {0.0};
-                if (valid) {
-                    C<double> acc[12], q[12], d[12];
-                    hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
-                    SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
-                    xpay_site(q, acc, L.kappa);
-                    SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+                    const bool on = s < L.g.V;
+                    C<double> acc[6], q[6], d[6];
+                    hop64_half<RECON, true>(L, L.t, s, hh, on, acc);
+                    if (on) {
+                        load_part<F64, SiteHalf, false>(pt, L.t, L.g.Vs, s, q);
+                        xpay_site(q, acc, L.kappa);
+                        load_part<F64, SiteHalf, false>(pt, L.db, L.g.Vs, s, d);
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
-                    v[0] = norm2_of(d);
-                    SpinorIO<F64>::store(L.r, L.g.Vs, s, d);
+                        for (int k = 0; k < 6; ++k) d[k] = csub(d[k], q[k]);
+                        v[0] += norm2_of(d);
+                        store_part<F64>(pt, L.r, L.g.Vs, s, d);
+                    }
                 }
                 tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) {
                     Scalars &c = a.sc[l2];
@@ -320,6 +424,11 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
                     c.rmax2 = rt;
                     if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
                     else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+                    if (!c.active) {
+                        // x stays as it is: this update was the final check
+                        c.true_n2 = rt;
+                        a.lstate[2 * l2 + 1] = 1;
+                    }
                 });
             });
             if (!grid_barrier(a)) return;
@@ -353,34 +462,45 @@ __global__ void __launch_bounds__(kTile, 3) k_batched_cg(BatchArgs a) {
         if (!grid_barrier(a)) return;
     }
 
-    // ---- final FP64 check: t = D x, |b - t|^2 ; |db - D^dag t|^2
-    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+    // ---- final FP64 check, for lattices whose last step was not a reliable update that
+    // stopped them: t = D x, |b - t|^2 ; |db - D^dag t|^2
+    for_tiles_half(a, unchecked, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+        const SiteHalf pt{hh};
         double v[1] = {0.0};
-        if (valid) {
-            C<double> acc[12], p[12], b[12];
-            hopping<F64, RECON, false, false>(L.g, L.x, L.g64, L.gdir64, s, acc);
-            SpinorIO<F64>::template load<false>(L.x, L.g.Vs, s, p);
-            xpay_site(p, acc, L.kappa);
-            SpinorIO<F64>::store(L.t, L.g.Vs, s, p);
-            SpinorIO<F64>::template load<false>(L.b, L.g.Vs, s, b);
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+            const bool on = s < L.g.V;
+            C<double> acc[6], p[6], bb[6];
+            hop64_half<RECON, false>(L, L.x, s, hh, on, acc);
+            if (on) {
+                load_part<F64, SiteHalf, false>(pt, L.x, L.g.Vs, s, p);
+                xpay_site(p, acc, L.kappa);
+                store_part<F64>(pt, L.t, L.g.Vs, s, p);
+                load_part<F64, SiteHalf, false>(pt, L.b, L.g.Vs, s, bb);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) b[c] = csub(b[c], p[c]);
-            v[0] = norm2_of(b);
+                for (int k = 0; k < 6; ++k) bb[k] = csub(bb[k], p[k]);
+                v[0] += norm2_of(bb);
+            }
         }
         tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) { a.sc[l2].true_b2 = t[0]; });
     });
     if (!grid_barrier(a)) return;
-    for_tiles(a, all, [&](const LatDesc &L, int g, int l, int s, bool valid) {
+    for_tiles_half(a, unchecked, [&](const LatDesc &L, int g, int l, int sl, int hh) {
+        const SiteHalf pt{hh};
         double v[1] = {0.0};
-        if (valid) {
-            C<double> acc[12], q[12], d[12];
-            hopping<F64, RECON, true, false>(L.g, L.t, L.g64, L.gdir64, s, acc);
-            SpinorIO<F64>::template load<false>(L.t, L.g.Vs, s, q);
-            xpay_site(q, acc, L.kappa);
-            SpinorIO<F64>::template load<false>(L.db, L.g.Vs, s, d);
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int s = (g - L.tile0) * kTile + h2 * kHalfTile + sl;
+            const bool on = s < L.g.V;
+            C<double> acc[6], q[6], d[6];
+            hop64_half<RECON, true>(L, L.t, s, hh, on, acc);
+            if (on) {
+                load_part<F64, SiteHalf, false>(pt, L.t, L.g.Vs, s, q);
+                xpay_site(q, acc, L.kappa);
+                load_part<F64, SiteHalf, false>(pt, L.db, L.g.Vs, s, d);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) d[c] = csub(d[c], q[c]);
-            v[0] = norm2_of(d);
+                for (int k = 0; k < 6; ++k) d[k] = csub(d[k], q[k]);
+                v[0] += norm2_of(d);
+            }
         }
         tile_reduce<1>(a, L, g, l, v, [&](int l2, const double *t) { a.sc[l2].true_n2 = t[0]; });
     });
@@ -482,12 +602,13 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     }
     // batch-wide buffers live in the first context
     cudaStream_t st = c0->stream;
-    void *d_lat, *d_sc, *d_cnt, *d_part, *d_tl, *d_bar;
+    void *d_lat, *d_sc, *d_cnt, *d_part, *d_tl, *d_bar, *d_lst;
     wd_status s;
     if ((s = ws_get(c0, "bt_lat", sizeof(LatDesc) * n, &d_lat)) != WD_OK) return s;
     if ((s = ws_get(c0, "bt_sc", sizeof(Scalars) * n, &d_sc)) != WD_OK) return s;
     if ((s = ws_get(c0, "bt_cnt", sizeof(unsigned) * n, &d_cnt)) != WD_OK) return s;
-    if ((s = ws_get(c0, "bt_part", sizeof(double) * 2 * ntiles, &d_part)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_part", sizeof(double) * kPart * ntiles, &d_part)) != WD_OK) return s;
+    if ((s = ws_get(c0, "bt_lstate", sizeof(int) * 2 * n, &d_lst)) != WD_OK) return s;
     if ((s = ws_get(c0, "bt_tl", sizeof(int) * ntiles, &d_tl)) != WD_OK) return s;
     if ((s = ws_get(c0, "bt_bar", 256, &d_bar)) != WD_OK) return s;
     std::vector<Scalars> h(n);
@@ -520,6 +641,7 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     a.bar_count = (unsigned *)d_bar;
     a.bar_gen = (unsigned *)d_bar + 16;
     a.flags = (int *)d_bar + 32;
+    a.lstate = (int *)d_lst;
     const char *stall = getenv("WD_BATCH_STALL_TEST");
     a.stall_test = stall && std::strcmp(stall, "1") == 0;
     // about one second at GB300 clocks; a tenth of that for the stalled-wait test

@@ -107,3 +107,50 @@ def test_batched_link_compression_rules(wd):
     lats[2].set_link_compression(1, 18)
     res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
     assert st == 0
+
+
+def oracle_residuals(U, b, x, kappa, dims):
+    """(||b - D x|| / ||b||, ||D^dag (b - D x)|| / ||D^dag b||) with the oracle's operator."""
+    r = b - oracle.apply_D(U, x, kappa, dims)
+    db = oracle.apply_Ddag(U, b, kappa, dims)
+    return (float(np.linalg.norm(r) / np.linalg.norm(b)),
+            float(np.linalg.norm(oracle.apply_Ddag(U, r, kappa, dims)) / np.linalg.norm(db)))
+
+
+def test_batched_mixed_start_vectors(wd):
+    """Zero and nonzero start vectors in one batch: each lattice takes its own setup path,
+    converges to the oracle's solution, and reports the oracle's residuals of its x."""
+    lats, kappas, bs, xs, inputs = make_batch(wd)
+    starts = {}
+    for i in (1, 4, 6):
+        U, b = inputs[i]
+        x_ref, _ = oracle.cgnr(U, b, kappas[i], lats[i].dims, tol=1e-13)
+        starts[i] = 0.5 * x_ref if i != 6 else gen.gaussian_source(lats[i].dims, seed=300)
+        xs[i] = lats[i].pack(starts[i])
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 0, res
+    for i, (lat, (U, b)) in enumerate(zip(lats, inputs)):
+        x = lat.unpack(xs[i])
+        x_ref, _ = oracle.cgnr(U, b, kappas[i], lat.dims, tol=1e-13)
+        assert oracle.rel_err(x, x_ref) < 1e-9, i
+        rb, rn = oracle_residuals(U, b, x, kappas[i], lat.dims)
+        assert res[i]["true_rel_resid"] == pytest.approx(rn, rel=1e-3), i
+        assert res[i]["true_rel_resid_b"] == pytest.approx(rb, rel=1e-3), i
+    # a start at half the solution needs fewer iterations than the zero start of the same lattice
+    lats2, kappas2, bs2, xs2, _ = make_batch(wd)
+    res0, _ = wd.cg_batched(lats2, kappas2, bs2, xs2, tol=1e-10, inner=1)
+    assert res[1]["iters"] <= res0[1]["iters"] and res[4]["iters"] <= res0[4]["iters"]
+
+
+def test_batched_iteration_limit_reports_residual_of_x(wd):
+    """Stopped by max_iter: WD_ERR_NOT_CONVERGED, and the reported residuals are those of
+    the returned x (the stopping reliable update doubles as the final check)."""
+    lats, kappas, bs, xs, inputs = make_batch(wd)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, max_iter=6, inner=1)
+    assert st == 4
+    for i, (lat, (U, b)) in enumerate(zip(lats, inputs)):
+        assert res[i]["status"] == 4 and res[i]["iters"] == 6 and res[i]["reliable_updates"] >= 1
+        rb, rn = oracle_residuals(U, b, lat.unpack(xs[i]), kappas[i], lat.dims)
+        assert rn > 1e-10
+        assert res[i]["true_rel_resid"] == pytest.approx(rn, rel=1e-6), i
+        assert res[i]["true_rel_resid_b"] == pytest.approx(rb, rel=1e-6), i
