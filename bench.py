@@ -333,7 +333,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eo", action="store_true", help="even-odd preconditioned solve")
-    ap.add_argument("--sweep", action="store_true", help="also time the Dslash at 8^4, 12^4, 16^4, 24^4")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the autotuned Dslash of every precision at 8^4, 12^4, 16^4, 24^4")
     ap.add_argument("--dslash-only", default=None, metavar="LX,LY,LZ,LT",
                     help="time only the Dslash kernel on this lattice (profiling helper)")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
@@ -717,7 +718,8 @@ def sweep(wd, torch, flush, stream, recon):
         lat.set_gauge(gen.haar_links(dims, 3), recon=recon)
         b = gen.gaussian_source(dims, 4)
         row = {}
-        for prec, pid in (("f64", 0), ("f32", 1), ("f16", 2)):
+        for prec, pid in (("f64", 0), ("f32", 1), ("f16", 2), ("df32", 3)):
+            tiles = lat.autotune(pid, 1)
             fi = lat.pack(b, pid)
             fo = lat.new_field(pid)
             for _ in range(3):
@@ -735,7 +737,8 @@ def sweep(wd, torch, flush, stream, recon):
             ms = statistics.mean(ts)
             V = lat.V
             row[prec] = {"ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V / ms / 1e6, 1),
-                         "gbs": round(V * dslash_bytes(prec, recon) / ms / 1e6, 1)}
+                         "gbs": round(V * dslash_bytes(prec, recon) / ms / 1e6, 1),
+                         "site_tile": tiles[0]}
         out[f"{L}^4"] = row
         lat.close()
     return out
