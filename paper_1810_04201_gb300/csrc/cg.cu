@@ -199,7 +199,10 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
             h[r].status = WD_ERR_NOT_CONVERGED;
         }
         WD_CUDA(c, cudaMemcpyAsync(f.sc, h.data(), sizeof(Scalars) * nrhs, cudaMemcpyHostToDevice, c->stream));
-        WD_CUDA(c, cudaMemsetAsync(f.state, 0, 3 * sizeof(int), c->stream));
+        // state: [0] loop bodies, [1] reliable updates run, [2] nonzero x0, [3] rows stopped
+        // at a reliable update, [4] final check needed (bytes 0x01: nonzero)
+        WD_CUDA(c, cudaMemsetAsync(f.state, 0, 4 * sizeof(int), c->stream));
+        WD_CUDA(c, cudaMemsetAsync(f.state + 4, 1, sizeof(int), c->stream));
         EventPair ev;
         WD_CUDA(c, ev.create());
         cudaEvent_t e0 = ev.e0, e1 = ev.e1;

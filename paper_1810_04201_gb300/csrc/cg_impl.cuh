@@ -138,7 +138,14 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
                 DslashArgs r = base;
                 r.mask = 2;
                 r.in = f.x; r.out = f.t;
-                add_op<F64, RECON, OP1, EpXpay, EO>(ib, r, pl.t64, false, f);
+                if constexpr (!EO && !NE) {
+                    // t = D x with |b - t|^2: an update that stops a row is its final check
+                    r.a0 = f.b;
+                    add_op<F64, RECON, OP1, EpTrue1, EO>(ib, r, pl.t64, true, f);
+                    r.a0 = nullptr;
+                } else {
+                    add_op<F64, RECON, OP1, EpXpay, EO>(ib, r, pl.t64, false, f);
+                }
                 r.in = f.t; r.a0 = f.db; r.a1 = f.r;
                 add_op<F64, RECON, OP2, EpReliable, EO>(ib, r, pl.t64, true, f);
                 v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
@@ -194,6 +201,9 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
         dbt = f.p;
     }
     a.in = xf; a.out = tf; a.a0 = bf;
+    // mixed precision on the full lattice: skipped when every row stopped at a reliable
+    // update, which computed these norms for the x it returns (state[4] = 0)
+    if (mixed && !EO && !NE) a.run_flag = f.state + 4;
     add_dslash<F64, RECON, false, EpTrue1>(gb, a, pl.t64, true);
     a.in = tf; a.a0 = dbt;
     add_dslash<F64, RECON, true, EpTrue2>(gb, a, pl.t64, true);

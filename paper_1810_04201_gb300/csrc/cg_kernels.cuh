@@ -252,6 +252,14 @@ struct EpReliable {
             c.rmax2 = rt;
             if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
             else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
+            if (!c.active && a.state) {
+                // this update checked the x the row returns: state[3] counts such rows, and
+                // state[4] (the final check's run flag where a plan allows) drops to 0
+                // once every row has stopped this way
+                c.true_n2 = rt;
+                a.state[3] += 1;
+                a.state[4] = a.state[3] < a.nrhs;
+            }
         });
     }
 };

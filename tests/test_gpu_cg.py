@@ -450,3 +450,41 @@ def test_multi_rhs_with_compressed_inner_links(wd):
         for j in range(3):
             x_ref, _ = ref_solution(U, B[j], kappa, dims)
             assert oracle.rel_err(X[j], x_ref) < 1e-9, (eo, j)
+
+
+def oracle_residuals(U, b, x, kappa, dims):
+    """(||b - D x|| / ||b||, ||D^dag (b - D x)|| / ||D^dag b||) with the oracle's operator."""
+    r = b - oracle.apply_D(U, x, kappa, dims)
+    db = oracle.apply_Ddag(U, b, kappa, dims)
+    return (float(np.linalg.norm(r) / np.linalg.norm(b)),
+            float(np.linalg.norm(oracle.apply_Ddag(U, r, kappa, dims)) / np.linalg.norm(db)))
+
+
+@pytest.mark.parametrize("inner", [1, 2, 3])
+@pytest.mark.parametrize("max_iter", [10000, 7])
+def test_mixed_reported_residuals_are_those_of_x(wd, inner, max_iter):
+    """Mixed precision on the full lattice: when every right-hand side stops at a reliable
+    update, that update is the final check.  The residuals reported must still be those of
+    the returned x, recomputed here with the oracle's operator; a zero source among the rows
+    (stopped at the setup) makes the final check run for all of them."""
+    dims, kappa = (4, 6, 4, 8), 0.12
+    U = gen.haar_links(dims, seed=21)
+    B = gen.gaussian_source(dims, seed=22, nrhs=3)
+    B[2] = 0.0
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    for rows in (2, 3):
+        fb, fx = lat.pack(B[:rows]), lat.new_field(nrhs=rows)
+        res, st = lat.cg(kappa, fb, fx, tol=1e-10, nrhs=rows, inner=inner, max_iter=max_iter,
+                         raise_on_fail=False)
+        X = lat.unpack(fx, nrhs=rows, squeeze=False)
+        assert st == (0 if max_iter > 100 else 4), res
+        for j in range(2):
+            rb, rn = oracle_residuals(U, B[j], X[j], kappa, dims)
+            tol = 1e-3 if max_iter > 100 else 1e-6
+            assert res[j]["true_rel_resid"] == pytest.approx(rn, rel=tol), (rows, j)
+            assert res[j]["true_rel_resid_b"] == pytest.approx(rb, rel=tol), (rows, j)
+            if max_iter > 100:
+                assert rn <= 1.01e-10
+        if rows == 3:
+            assert not X[2].any() and res[2]["true_rel_resid"] == 0.0
