@@ -219,12 +219,15 @@ typedef struct wd_cg_params {
     int precondition;
 } wd_cg_params;
 
-/* Per right-hand side result. */
+/* Per right-hand side result.  The two residuals are recomputed from the returned x
+ * with the FP64 operator: by a final check after the loop, or, where a mixed-precision
+ * solve on the full lattice (or a batched lattice) stopped at a reliable update, by
+ * that update, which computed D x and D^dag(b - D x) for the same x. */
 typedef struct wd_cg_result {
     int iters;               /* CG iterations */
     int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
-    double true_rel_resid;   /* ||D^dag(b - D x)|| / ||D^dag b||, recomputed in FP64 at the end */
-    double true_rel_resid_b; /* ||b - D x|| / ||b||, recomputed in FP64 at the end */
+    double true_rel_resid;   /* ||D^dag(b - D x)|| / ||D^dag b|| of the returned x, in FP64 */
+    double true_rel_resid_b; /* ||b - D x|| / ||b|| of the returned x, in FP64 */
     double seconds;          /* device time of the solve */
     int status;              /* wd_status of this right-hand side */
 } wd_cg_result;
@@ -247,7 +250,8 @@ wd_status wd_cg_solve_canonical(wd_ctx *ctx, double kappa, const double *b_canon
 
 /* Solve n independent lattices, each with its own context (dims, gauge field) and
  * kappa, in one persistent cooperative kernel launch, with mixed-precision
- * (inner_prec) CG and FP64 reliable updates.  All contexts must live on the same
+ * (inner_prec) CG and FP64 reliable updates; x[i] holds lattice i's start vector
+ * (an all-zero one skips the setup's operator applications on it).  All contexts must live on the same
  * device; the work runs on ctxs[0]'s stream.  b[i], x[i]: WD_F64 fields of ctxs[i]
  * (one right-hand side); result[i] receives lattice i's result.  Every context needs
  * the same pair of link compressions (FP64, inner precision), a pair that
