@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the bench's CPU
 baseline use this package; the CUDA library never does and shares no code
 with it.  The arithmetic lives in ``wilson_oracle.c`` (plain C99, FP64,
 complex.h); this module compiles it with gcc, loads it through ctypes and adds
-the dense-matrix checks (numpy / LAPACK).
+the dense-matrix checks (numpy / LAPACK) and a Lanczos estimate of the extreme
+eigenvalues of D^dag D (the condition number that bounds solution errors).
 
 Paper passages followed (arXiv:1810.04201):
   * section 2.1, Eq. (1)-(3): the operator D, kappa, the projectors 1 +- gamma_mu;
@@ -171,6 +172,38 @@ def dense_solve(U, b, kappa, dims, antiperiodic_t=True):
     M = dense_matrix(U, kappa, dims, antiperiodic_t)
     x = np.linalg.solve(M, _c128(b).reshape(-1))
     return x.reshape(np.shape(b))
+
+
+def normal_extreme_eigs(U, kappa, dims, steps, seed=0, antiperiodic_t=True):
+    """Estimates of the smallest and largest eigenvalues of D^dag D (hermitian, positive;
+    section 2.2), which bound the error of a CG solution: ||x - x*|| / ||x*|| <=
+    cond(D) ||b - D x|| / ||b||, cond(D) = sqrt(lambda_max / lambda_min).
+
+    Plain Lanczos without reorthogonalisation from a seeded Gaussian start vector: the
+    extreme eigenvalues of the k-step tridiagonal matrix (diagonal alpha_j, off-diagonal
+    beta_j) approach those of D^dag D from inside as k grows; lost orthogonality only adds
+    copies of eigenvalues that have already converged.  Returns (lambda_min, lambda_max,
+    steps taken)."""
+    from scipy.linalg import eigh_tridiagonal
+    v = int(np.prod(dims))
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal((v, 4, 3)) + 1j * rng.standard_normal((v, 4, 3))
+    q /= np.linalg.norm(q)
+    q_prev = np.zeros_like(q)
+    beta = 0.0
+    alphas, betas = [], []
+    for _ in range(steps):
+        w = apply_normal(U, q, kappa, dims, antiperiodic_t)
+        alpha = float(np.vdot(q, w).real)
+        w -= alpha * q + beta * q_prev
+        alphas.append(alpha)
+        beta = float(np.linalg.norm(w))
+        if beta == 0.0:
+            break
+        betas.append(beta)
+        q_prev, q = q, w / beta
+    ev = eigh_tridiagonal(np.array(alphas), np.array(betas[:len(alphas) - 1]), eigvals_only=True)
+    return float(ev[0]), float(ev[-1]), len(alphas)
 
 
 def rel_err(a, b) -> float:

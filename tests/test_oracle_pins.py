@@ -307,3 +307,21 @@ def test_paper_stencil_byte_count():
     assert (9 * spinor_reals + 8 * link_reals) * 8 == vals["stencil_input_bytes"]
     # 16 SU(3) x colour-vector products, each 9 complex multiply-adds of 8 flops (section 6.4, stage 3)
     assert 16 * 9 * 8 == vals["su3_mult_flops"]
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 2, 4)])
+def test_lanczos_extremes_match_dense_spectrum(dims):
+    """The Lanczos estimate of the extreme eigenvalues of D^dag D (the condition-number
+    bound on CG solution errors) against LAPACK's eigenvalues of the assembled D^dag D:
+    exact once the steps reach the dimension, and inside the spectrum before that
+    (Ritz values interlace)."""
+    U = gen.haar_links(dims, seed=31)
+    M = oracle.dense_matrix(U, 0.12, dims)
+    ev = np.linalg.eigvalsh(M.conj().T @ M)
+    n = M.shape[0]
+    lo, hi, k = oracle.normal_extreme_eigs(U, 0.12, dims, steps=n, seed=5)
+    assert k == n
+    assert lo == pytest.approx(ev[0], rel=1e-8) and hi == pytest.approx(ev[-1], rel=1e-10)
+    lo, hi, k = oracle.normal_extreme_eigs(U, 0.12, dims, steps=n // 6, seed=5)
+    assert ev[0] * (1 - 1e-12) <= lo and hi <= ev[-1] * (1 + 1e-12)
+    assert hi > 0.9 * ev[-1]
