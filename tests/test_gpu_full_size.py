@@ -10,6 +10,8 @@ residual D^dag (b - D x) that CGNR stops on), which holds at any size.
             even-odd preconditioning (the fastest mixed-precision variants)
   24^3x48   Haar links, kappa = 0.12: the 12 spin-colour point sources in one multi-RHS solve
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -17,6 +19,8 @@ import oracle
 from paper_1810_04201_gb300 import gen
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -79,3 +83,54 @@ def test_c4_multi_rhs_point_sources_residual(wd):
     for j in (0, 5, 11):
         _, rn = normal_residual(U, B[j], X[j], kappa, dims)
         assert rn <= 1.01e-10, j
+
+
+def read_c3_reference():
+    """The oracle's 32^3 x 64 solution at sampled sites and its error-bound data
+    (tests/golden/c3_oracle_reference.txt, written by make_c3_reference.py there)."""
+    meta, sites, vals = {}, [], []
+    for line in open(os.path.join(GOLDEN, "c3_oracle_reference.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        if parts[0] == "site":
+            sites.append(int(parts[1]))
+            r = np.array(parts[2:], dtype=np.float64)
+            vals.append((r[0::2] + 1j * r[1::2]).reshape(4, 3))
+        else:
+            meta[parts[0]] = float(parts[1])
+    return meta, np.array(sites), np.array(vals)
+
+
+# (inner precision, even-odd, inner-precision link compression); inner 0 is plain FP64 CG
+C3_VARIANTS = [(0, 0, 18), (1, 0, 18), (2, 0, 18), (3, 0, 18), (0, 1, 18), (1, 1, 18), (2, 1, 18), (3, 1, 18),
+               (1, 1, 12)]
+
+
+def test_c3_variants_against_oracle_solution(wd):
+    """Each 32^3 x 64 solver variant against the oracle's solution (CG to 1e-13): the error at
+    the sampled sites, over the norm of the whole oracle solution, stays below the forward-error
+    bound cond(D) ||b - D x|| / ||b|| (cond(D) from the oracle's Lanczos estimate of the spectrum
+    of D^dag D).  Prints the sampled estimate of each variant's relative error."""
+    meta, sites, xref = read_c3_reference()
+    dims, kappa = (32, 32, 32, 64), 0.124
+    U = gen.smoothed_links(dims, 6, eps=0.4)
+    b = gen.gaussian_source(dims, 6)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb = lat.pack(b)
+    scale = np.sqrt(lat.V / len(sites))
+    for inner, eo, rin in C3_VARIANTS:
+        if inner:
+            lat.set_link_compression(inner, rin)
+        fx = lat.new_field()
+        res, st = lat.cg(kappa, fb, fx, tol=1e-10, inner=inner, precondition=eo)
+        assert st == 0 and res[0]["true_rel_resid"] <= 1e-10
+        x = lat.unpack(fx)
+        err = float(np.linalg.norm(x[sites] - xref) / meta["x_norm"])
+        bound = meta["cond_D"] * res[0]["true_rel_resid_b"]
+        print(f"C3 inner={inner} eo={eo} recon_inner={rin}: ||b-Dx||/||b|| {res[0]['true_rel_resid_b']:.3e}, "
+              f"sampled relative error {err * scale:.3e} (estimate), bound {bound:.3e}")
+        assert err <= bound, (inner, eo, rin, err, bound)
+        if inner:
+            lat.set_link_compression(inner, 18)
