@@ -6,7 +6,7 @@ antiperiodic t.  The oracle solves D^dag D x = D^dag b by CG (section 2.2) to a 
 residual of 1e-13; the extreme eigenvalues of D^dag D come from the oracle's Lanczos
 estimate.  Every value written here comes from oracle/ (no GPU involved).
 
-Run from the repository root (about 20 minutes on 8 cores):
+Run from the repository root (about an hour on 8 cores):
     python tests/golden/make_c3_reference.py
 """
 import os
