@@ -5,7 +5,8 @@ projector sign, U where U^dag belongs, a transposed link, a dropped
 antiperiodic sign, a wrong link site, a dropped hop, a wrong kappa sign, a typo
 in a gamma matrix, norms where squared norms belong in CG), builds it, and
 checks that at least one of the pins used in test_oracle_pins fails for it.
-The unmodified source passes all of them.
+The unmodified source passes all of them.  The Lanczos estimate of the
+spectrum of D^dag D (Python) gets the same treatment with its own pin.
 """
 import ctypes
 import os
@@ -160,3 +161,43 @@ def test_mutation_is_caught(tmp_path, name, monkeypatch):
         assert ok
     else:
         assert not ok, f"mutation {name} passed every pin"
+
+
+# The same for the oracle's Lanczos estimate of the spectrum of D^dag D: each case plants one
+# mistake in a copy of the Python function and checks that its pin (the extreme eigenvalues
+# of the assembled D^dag D from LAPACK) fails.
+LANCZOS_MUTATIONS = {
+    "clean": None,
+    "two_term_recurrence": ("w -= alpha * q + beta * q_prev", "w -= alpha * q"),
+    "shifted_offdiagonal": ("np.array(betas[:len(alphas) - 1])", "np.array(betas[1:len(alphas)])"),
+    "unnormalised_vector": ("q_prev, q = q, w / beta", "q_prev, q = q, w"),
+}
+
+
+def lanczos_variant(mut):
+    import inspect
+    import oracle
+    src = inspect.getsource(oracle.normal_extreme_eigs)
+    if mut is not None:
+        assert mut[0] in src
+        src = src.replace(mut[0], mut[1])
+    ns = dict(vars(oracle))
+    exec(src, ns)
+    return ns["normal_extreme_eigs"]
+
+
+@pytest.mark.parametrize("name", list(LANCZOS_MUTATIONS))
+def test_lanczos_mutation_is_caught(name):
+    import oracle
+    fn = lanczos_variant(LANCZOS_MUTATIONS[name])
+    dims = (2, 2, 2, 2)
+    U = gen.haar_links(dims, seed=31)
+    M = oracle.dense_matrix(U, 0.12, dims)
+    ev = np.linalg.eigvalsh(M.conj().T @ M)
+    with np.errstate(all="ignore"):
+        lo, hi, _ = fn(U, 0.12, dims, steps=M.shape[0], seed=5)
+    ok = bool(np.isclose(lo, ev[0], rtol=1e-8) and np.isclose(hi, ev[-1], rtol=1e-10))
+    if name == "clean":
+        assert ok
+    else:
+        assert not ok, f"mutation {name} passed the pin"
