@@ -322,7 +322,7 @@ wd_status wd_pack(wd_ctx *c, const double *canon, int on_device, void *field, wd
     if (!c) return WD_ERR_ARG;
     if (!canon || !field || bad_prec(prec) || nrhs < 1 || nrhs > WD_MAX_RHS)
         return fail(c, WD_ERR_ARG, "wd_pack: bad argument");
-    const double *src;
+    const double *src = nullptr;
     wd_status s = canon_stage(c, canon, nrhs, on_device, &src);
     if (s != WD_OK) return s;
     VecArgs v{};

@@ -39,7 +39,7 @@ struct GraphBuilder {
     }
 };
 
-static cudaError_t add_chain(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, const std::vector<KCall> &calls) {
+static inline cudaError_t add_chain(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, const std::vector<KCall> &calls) {
     for (const KCall &k : calls) {
         void *params[1] = {const_cast<unsigned char *>(k.arg.data())};
         cudaKernelNodeParams p{};
@@ -56,7 +56,7 @@ static cudaError_t add_chain(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, 
     return cudaSuccess;
 }
 
-static cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+static inline cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
                                    cudaGraphConditionalNodeType type, cudaGraph_t *body) {
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
@@ -71,7 +71,7 @@ static cudaError_t add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t> &
     return cudaSuccess;
 }
 
-static cudaError_t launch_chain(const std::vector<KCall> &calls, cudaStream_t st) {
+static inline cudaError_t launch_chain(const std::vector<KCall> &calls, cudaStream_t st) {
     for (const KCall &k : calls) {
         void *params[1] = {const_cast<unsigned char *>(k.arg.data())};
         cudaError_t e = cudaLaunchKernel(k.func, k.grid, k.block, params, 0, st);
@@ -80,7 +80,7 @@ static cudaError_t launch_chain(const std::vector<KCall> &calls, cudaStream_t st
     return cudaSuccess;
 }
 
-static int num_sms() {
+static inline int num_sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
