@@ -58,3 +58,28 @@ def test_sources_name_no_batched_memcpy():
     pat = re.compile("Memcpy" + "(3D)?" + "Batch")
     for n in os.listdir(d):
         assert not pat.search(open(os.path.join(d, n)).read()), n
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program that includes wd.h, takes the address of every declared function,
+    links against libwd.so and calls the entry points that need no GPU."""
+    import subprocess
+    from paper_1810_04201_gb300 import build
+    so = build.build()
+    names = declared()
+    prog = ["#include <stdio.h>", '#include "wd.h"', "int main(void) {",
+            "    void *fns[] = {" + ", ".join(f"(void *)&{n}" for n in names) + "};",
+            "    int dims[4] = {4, 1, 4, 4};",
+            "    wd_ctx *ctx = 0;",
+            "    if (wd_create(&ctx, dims, 1, 0) != WD_ERR_ARG) return 1;",
+            "    if (!wd_status_string(WD_OK)) return 2;",
+            '    printf("%d %s\\n", (int)(sizeof fns / sizeof fns[0]), wd_status_string(WD_ERR_ARG));',
+            "    return 0;", "}"]
+    c = tmp_path / "abi_check.c"
+    c.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "abi_check"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe),
+                    "-L", os.path.dirname(so), "-lwd", "-Wl,-rpath," + os.path.dirname(so)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == len(names)
