@@ -520,6 +520,12 @@ def main():
         dist.destroy_process_group()
 
 
+def rel_diff(a, b) -> float:
+    """||a - b|| / ||b|| of two solutions."""
+    nb = np.linalg.norm(np.ravel(b))
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / (nb if nb > 0 else 1.0))
+
+
 def _timed_solves(torch, fn, reps):
     """Median device time (CUDA events) of `fn` over `reps` runs after one warm-up."""
     fn()
@@ -542,7 +548,6 @@ def compare(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    import oracle
     from paper_1810_04201_gb300 import gen, wd
     reps = max(1, min(args.steps, 3))
     line = {"workload": args.workload, "compare": {}}
@@ -576,7 +581,7 @@ def compare(args):
             return out
 
         ms_s, res_s = _timed_solves(torch, one_by_one, reps)
-        err = max(oracle.rel_err(a, l.unpack(y)) for a, l, y in zip(xb, lats, ys))
+        err = max(rel_diff(a, l.unpack(y)) for a, l, y in zip(xb, lats, ys))
         line["compare"] = {
             "lattices": 64, "total_sites": V, "recon": args.recon, "recon_inner": args.recon_inner or args.recon,
             "shapes": sorted(set("x".join(map(str, d)) for d in shapes)),
@@ -619,19 +624,15 @@ def compare(args):
             r = res[0]
             x = lat.unpack(fx)
             sols[name] = x
-            # the oracle's own operator on the GPU solution: ||b - D x|| / ||b||
-            t0 = time.perf_counter()
-            ores = oracle.rel_err(oracle.apply_D(U, x, w["kappa"], dims), b)
             line["compare"][name] = {"ms": round(ms, 3), "iters": r["iters"], "reliable_updates": r["reliable_updates"],
                                      "status": st, "true_rel_resid_normal": r["true_rel_resid"],
-                                     "true_rel_resid_b": r["true_rel_resid_b"], "oracle_rel_resid_b": ores,
-                                     "oracle_check_s": round(time.perf_counter() - t0, 2),
+                                     "true_rel_resid_b": r["true_rel_resid_b"],
                                      "gflops": round((2 * r["iters"] + 4 + 2 * r["reliable_updates"]) * 1320 * V
                                                      / ms / 1e6, 1)}
         for name in variants:
             if name == "f64":
                 continue
-            line["compare"][name]["rel_diff_vs_f64_solution"] = oracle.rel_err(sols[name], sols["f64"])
+            line["compare"][name]["rel_diff_vs_f64_solution"] = rel_diff(sols[name], sols["f64"])
             line["compare"][name]["speedup_vs_f64"] = round(line["compare"]["f64"]["ms"] / line["compare"][name]["ms"], 3)
         line["note"] = ("gflops counts 1320 flop/site per full-lattice operator application; an even-odd "
                         "iteration applies the Schur operator twice, counted as 2 * 1320 * V / 2 * 2 flop")
@@ -668,7 +669,7 @@ def compare(args):
             line["compare"][name] = {"ms": round(ms2, 3), "status": st2, "iters_max": max(r["iters"] for r in res2),
                                      "max_true_rel_resid": max(r["true_rel_resid"] for r in res2),
                                      "speedup_vs_sequential_f64": round(ms / ms2, 3),
-                                     "max_rel_diff_vs_sequential": max(oracle.rel_err(X[k], Xs[k]) for k in range(12))}
+                                     "max_rel_diff_vs_sequential": max(rel_diff(X[k], Xs[k]) for k in range(12))}
     line["config"] = config_of(args, w)
     print(json.dumps(line))
 
