@@ -3,7 +3,8 @@
 Each case plants one mistake in a copy of the oracle's C source (a flipped
 projector sign, U where U^dag belongs, a transposed link, a dropped
 antiperiodic sign, a wrong link site, a dropped hop, a wrong kappa sign, a typo
-in a gamma matrix, norms where squared norms belong in CG), builds it, and
+in a gamma matrix, norms where squared norms belong in CG, D where D^dag belongs
+in the recomputed normal residual, that residual divided by |b|), builds it, and
 checks that at least one of the pins used in test_oracle_pins fails for it.
 The unmodified source passes all of them.  The Lanczos estimate of the
 spectrum of D^dag D (Python) gets the same treatment with its own pin.
@@ -34,6 +35,10 @@ MUTATIONS = {
     "gamma2_typo": ("{{0, 0, I, 0}, {0, 0, 0, -I}, {-I, 0, 0, 0}, {0, I, 0, 0}}",
                     "{{0, 0, I, 0}, {0, 0, 0, I}, {-I, 0, 0, 0}, {0, I, 0, 0}}"),
     "cg_unsquared_norms": ("double alpha = rho / norm2(q, N);", "double alpha = sqrt(rho) / sqrt(norm2(q, N));"),
+    "residual_D_instead_of_Ddag": ("oracle_wilson_apply(L, ap, kappa, U, e, De, 1);",
+                                   "oracle_wilson_apply(L, ap, kappa, U, e, De, 0);"),
+    "normal_residual_over_norm_b": ("info->true_normal_rel = ndb > 0 ? sqrt(nde / ndb) : sqrt(nde);",
+                                    "info->true_normal_rel = nb > 0 ? sqrt(nde / nb) : sqrt(nde);"),
 }
 
 
@@ -144,6 +149,16 @@ def pins_pass(lib):
     # the operator itself must also be the true one: compare the dense solve with the CG result
     xd = np.linalg.solve(Mat, b2.reshape(-1)).reshape(b2.shape)
     if not (info.converged and rel(x, xd) < 1e-9):
+        return False
+    # the recomputed residuals of a far-from-converged x (three iterations) against numpy on Mat
+    x3 = np.zeros_like(b2)
+    i3 = Info()
+    lib.oracle_cgnr((ctypes.c_int * 4)(*d2), 1, 0.12, _p(U2), _p(b2), _p(x3), 1e-14, 3, ctypes.byref(i3))
+    r3 = b2.reshape(-1) - Mat @ x3.reshape(-1)
+    want_rel = np.linalg.norm(r3) / np.linalg.norm(b2)
+    want_normal = np.linalg.norm(Mat.conj().T @ r3) / np.linalg.norm(Mat.conj().T @ b2.reshape(-1))
+    if not (np.isclose(i3.true_rel, want_rel, rtol=1e-12) and np.isclose(i3.true_normal_rel, want_normal,
+                                                                          rtol=1e-12)):
         return False
     # CG's convergence bound: |r_k| / |r_0| <= 2 sqrt(K) ((sqrt(K) - 1) / (sqrt(K) + 1))^k, K = cond(D^dag D)
     sv = np.linalg.svd(Mat, compute_uv=False)

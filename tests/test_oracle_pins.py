@@ -289,6 +289,35 @@ def test_cgnr_initial_guess_resume():
     assert oracle.rel_err(xb, xc) < 1e-10
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 2, 4)])
+@pytest.mark.parametrize("case", ["cgnr_start_vector", "cgnr_three_steps", "cgne_three_steps"])
+def test_recomputed_residuals_match_dense_matrix(dims, case):
+    """The residuals the solvers report for the x they return (section 2.2: r = b - D x for the
+    system, D^dag r for the normal equations) against numpy on the assembled matrix M:
+    ||b - M x|| / ||b|| and ||M^H (b - M x)|| / ||M^H b||.  The x is far from converged (a random
+    start vector with no iteration, or three iterations), so the two residuals are O(1) and differ."""
+    kappa = 0.12
+    U = gen.haar_links(dims, seed=51)
+    b = gen.gaussian_source(dims, seed=52)
+    if case == "cgnr_start_vector":
+        x0 = gen.gaussian_source(dims, seed=53)
+        x, info = oracle.cgnr(U, b, kappa, dims, tol=1e-14, max_iter=0, x0=x0)
+        np.testing.assert_array_equal(x, x0)
+    elif case == "cgnr_three_steps":
+        x, info = oracle.cgnr(U, b, kappa, dims, tol=1e-14, max_iter=3)
+    else:
+        x, info = oracle.cgne(U, b, kappa, dims, tol=1e-14, max_iter=3)
+    assert not info["converged"]
+    M = oracle.dense_matrix(U, kappa, dims)
+    bf, xf = b.reshape(-1), x.reshape(-1)
+    r = bf - M @ xf
+    want_rel = np.linalg.norm(r) / np.linalg.norm(bf)
+    want_normal = np.linalg.norm(M.conj().T @ r) / np.linalg.norm(M.conj().T @ bf)
+    assert want_rel > 1e-3 and want_normal > 1e-3 and abs(want_rel / want_normal - 1) > 1e-3
+    assert info["true_rel"] == pytest.approx(want_rel, rel=1e-12)
+    assert info["true_normal_rel"] == pytest.approx(want_normal, rel=1e-12)
+
+
 def test_cg_zero_source():
     dims = (2, 2, 2, 2)
     U = gen.haar_links(dims, seed=1)
