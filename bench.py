@@ -3,20 +3,26 @@
 A step is one full CG solve of D x = b on the normal equations to a true FP64
 residual of 1e-10 (section 2.2), on seeded synthetic inputs:
 
-  c2 (default)  16^4, Haar-random SU(3) links, kappa = 0.12, Gaussian source,
-                plain FP64 CG
+  c3 (default)  32^3 x 64, smoothed links exp(i 0.4 H), kappa = 0.124, Gaussian
+                source, plain FP64 CGNR (the largest single-GPU workload)
+  c2            16^4, Haar-random SU(3) links, kappa = 0.12, Gaussian source
   c1            4^4, same recipe
-  c3            32^3 x 64, smoothed links exp(i 0.4 H), kappa = 0.124,
-                mixed precision (--inner f32|f16|f64, default f32)
   c4            24^3 x 48, Haar links, kappa = 0.12, the 12 spin-colour point
-                sources solved together (multi-RHS CG, --inner f64|f32)
+                sources solved together (multi-RHS CG)
+  (--inner f32|f16|df32 runs the step with that inner precision instead)
 
-value = GFLOP/s of the solve at 1320 flop per site per Dslash application
-(the Dslash flops of the 2 * iterations + 4 operator applications), i.e. the
-sustained Dslash rate inside the solver.  The roofline object describes the
-plain Dslash kernel of the solve's precision on the same lattice, timed alone.
+value = GFLOP/s of the solve at 1320 flop per site per Dslash application,
+counting the operator applications the solve performs (2 per iteration, D^dag b
+in the setup, the two of the final FP64 check; a zero start vector skips the
+setup's D x0 pair).  The roofline object describes the plain Dslash kernel of
+the step's precision on the same lattice, timed alone; for FP64 its roof is the
+FP64 multiply-add rate measured in the same run (wd_measure_fp64_rate).  The
+`cg` object times every solver variant on the same lattice and source (mixed
+precision, even-odd, compressed inner links, the system-residual stopping rule)
+against the FP64 step, and `multi_rhs` the 12 point sources of the 24^3 x 48
+workload solved together against 12 sequential FP64 solves.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
 """
 from __future__ import annotations
@@ -48,7 +54,7 @@ PREC_ID = {"f64": 0, "f32": 1, "f16": 2, "df32": 3}
 WORKLOADS = {
     "c1": dict(dims=(4, 4, 4, 4), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=1),
     "c2": dict(dims=(16, 16, 16, 16), links="haar", kappa=0.12, nrhs=1, inner="f64", seed=2),
-    "c3": dict(dims=(32, 32, 32, 64), links="smoothed", kappa=0.124, nrhs=1, inner="f32", seed=6),
+    "c3": dict(dims=(32, 32, 32, 64), links="smoothed", kappa=0.124, nrhs=1, inner="f64", seed=6),
     "c4": dict(dims=(24, 24, 24, 48), links="haar", kappa=0.12, nrhs=12, inner="f64", seed=7),
 }
 L2_FLUSH_BYTES = 512 << 20
@@ -67,8 +73,8 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# FP64 peak of a GB300 from the nominal figure (1.25 TFLOP/s dense FP64).
-FP64_PEAK_GFLOPS = 1250.0
+# Nominal FP64 rate of a GB300: 152 SMs x 2 FP64 FMAs per clock x 2 flop x 2.07 GHz.
+FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07
 
 
 # the sources that define the plain Dslash kernel (the one the roofline object reports)
@@ -247,9 +253,10 @@ def make_inputs(w, rank):
     return U, b
 
 
-def cpu_baseline(w, U, b, budget_s=20.0):
+def cpu_baseline(w, U, b, budget_s=20.0, one_core=True):
     """The oracle, as it stands, on a bounded sample of the same solve (a fixed number
-    of CG iterations on the same lattice and source)."""
+    of CG iterations on the same lattice and source), on all host cores; with one_core,
+    also the oracle operator's rate on one core, measured on a bounded sample of sites."""
     import oracle
     dims = w["dims"]
     V = int(np.prod(dims))
@@ -263,20 +270,21 @@ def cpu_baseline(w, U, b, budget_s=20.0):
     t0 = time.perf_counter()
     _, info = oracle.cgnr(U, b1, w["kappa"], dims, tol=1e-10, max_iter=iters)
     t = time.perf_counter() - t0
-    n_apply = 2 * info["iters"] + 5  # setup 2, per iteration 2, true residual 3
+    n_apply = 2 * info["iters"] + 5  # setup 2, per iteration 2, recomputed residuals 3
     gflops = n_apply * FLOP_PER_SITE * V / t / 1e9
-    # the same operator on one core, for the per-core rate
-    oracle.set_threads(1)
-    t0 = time.perf_counter()
-    oracle.apply_D(U, b1, w["kappa"], dims)
-    t1 = time.perf_counter() - t0
-    oracle.set_threads(threads)
-    return {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-            "sample": f"oracle CGNR on the same {'x'.join(map(str, dims))} lattice and source, "
-                      f"{info['iters']} iterations ({n_apply} operator applications) in {t:.1f} s, "
-                      f"{threads} OpenMP threads; 1320 flop/site per application",
-            "dslash_gflops_all_cores": round(FLOP_PER_SITE * V / t_apply / 1e9, 4),
-            "dslash_gflops_one_core": round(FLOP_PER_SITE * V / t1 / 1e9, 4)}
+    out = {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+           "sample": f"oracle CGNR on the same {'x'.join(map(str, dims))} lattice and source, "
+                     f"{info['iters']} iterations ({n_apply} operator applications) in {t:.1f} s, "
+                     f"{threads} OpenMP threads; 1320 flop/site per application",
+           "dslash_gflops_all_cores": round(FLOP_PER_SITE * V / t_apply / 1e9, 4)}
+    if one_core:
+        # the operator on one core, at the first min(V, 65536) sites
+        sites = np.arange(min(V, 65536), dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.apply_D_sites(U, b1, w["kappa"], dims, sites)
+        t1 = time.perf_counter() - t0
+        out["dslash_gflops_one_core"] = round(FLOP_PER_SITE * len(sites) / t1 / 1e9, 4)
+    return out
 
 
 def run_reference(args, w, rank, world):
@@ -285,12 +293,12 @@ def run_reference(args, w, rank, world):
         return
     U, b = make_inputs(w, 0)
     for _ in range(args.warmup):
-        cpu_baseline(w, U, b, budget_s=2.0)
+        cpu_baseline(w, U, b, budget_s=2.0, one_core=False)
     vals = []
     t0 = time.perf_counter()
     last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(w, U, b, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+    for k in range(args.steps):
+        last = cpu_baseline(w, U, b, budget_s=max(2.0, 60.0 / max(args.steps, 1)), one_core=k == args.steps - 1)
         vals.append(last["value"])
     el = time.perf_counter() - t0
     v = float(np.mean(vals))
@@ -319,18 +327,34 @@ def config_of(args, w):
             "parallelism": "replicas (one independent lattice per GPU)"}
 
 
+def operator_applications(r, inner: str, eo: bool) -> int:
+    """Full-lattice operator applications (1320 flop/site each) of one solve from a zero
+    start vector: D^dag b in the setup, 2 per iteration, 2 per FP64 reliable update and
+    the two of the final FP64 check (the D x0 pair is skipped).  A mixed-precision CGNR
+    solve that stopped at a reliable update uses that update as its final check.  An
+    even-odd iteration applies the Schur operator twice: 4 half-lattice hops, counted as
+    2 full-lattice applications."""
+    n = 2 * r["iters"] + 1 + 2 * r["reliable_updates"]
+    if inner == "f64" or eo:
+        n += 2
+    return n
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wd", choices=["wd", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS) + ["c5"])
     ap.add_argument("--inner", default=None, choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--recon", type=int, default=18, choices=[18, 12, 8])
     ap.add_argument("--recon-inner", type=int, default=None, choices=[18, 12, 8],
                     help="link compression of the inner precision's copy (default: --recon)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the step and its Dslash only (no solver variants, multi-RHS block, e2e or CPU "
+                         "baseline): the profiling pass")
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eo", action="store_true", help="even-odd preconditioned solve")
     ap.add_argument("--sweep", action="store_true",
@@ -422,7 +446,7 @@ def main():
         dist.barrier()
     total_ms = float(sum(times))
     iters = max(r["iters"] for r in results)
-    n_apply = 2 * iters + 4 + 2 * max(r["reliable_updates"] for r in results)
+    n_apply = max(operator_applications(r, inner, args.eo) for r in results)
     flops_step = n_apply * FLOP_PER_SITE * V * nrhs
 
     # ---- the Dslash kernel alone (same lattice, solve precision), CUDA events per launch
@@ -443,6 +467,9 @@ def main():
         torch.cuda.synchronize()
         dts.append(e0.elapsed_time(e1))
         launches += 1
+    # the FP64 roof, measured in the same run and under the same clock record
+    fp64_rate = wd.measure_fp64_rate()
+    launches += 6
     clk = clocks.stop()
     d_ms = statistics.mean(dts)
     d_gflops = FLOP_PER_SITE * V * nrhs / (d_ms * 1e-3) / 1e9
@@ -454,13 +481,14 @@ def main():
 
     # ---- end to end: canonical host buffers, copies inside the timed region
     e2e = None
-    if nrhs == 1:
+    if nrhs == 1 and not args.headline_only:
         bt = torch.from_numpy(np.ascontiguousarray(b)).pin_memory()
         xt = torch.zeros_like(bt).pin_memory()
         pc = 1 if args.eo else 0
         lat.cg_canonical(w["kappa"], bt, xt, tol=1e-10, inner=wd.PRECS[inner], delta=args.delta, precondition=pc)
         et = []
-        for _ in range(args.steps):
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
             flush.zero_()
             xt.zero_()
             torch.cuda.synchronize()
@@ -472,7 +500,8 @@ def main():
         e2e_s = float(np.mean(et))
         e2e = {"value": round(flops_step / e2e_s / 1e9, 3), "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(2 * bt.numel() * 16), "d2h_bytes_per_step": int(xt.numel() * 16),
-               "ms_per_step": round(e2e_s * 1e3, 3), "gpu_launches_per_step": int(launches_e2e)}
+               "ms_per_step": round(e2e_s * 1e3, 3), "steps": e2e_steps, "gpu_launches_per_step": int(launches_e2e),
+               "call": "wd_cg_solve_canonical on pinned host buffers (b and the zero start vector in, x out)"}
 
     # max over ranks
     step_ms = max_over_ranks(total_ms / args.steps, dist, "cuda")
@@ -484,9 +513,11 @@ def main():
         return
 
     if prec == "f64":
-        roof = {"bound": "alu", "achieved": round(d_gflops / 1e3, 4), "peak": FP64_PEAK_GFLOPS / 1e3,
-                "unit": "TFLOP/s", "frac": round(d_gflops / FP64_PEAK_GFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s; no FP64 entry in MEASURED_PEAKS.json)",
+        roof = {"bound": "alu", "achieved": round(d_gflops / 1e3, 4), "peak": round(fp64_rate / 1e3, 4),
+                "unit": "TFLOP/s", "frac": round(d_gflops / fp64_rate, 4),
+                "peak_source": "measured in this run: FP64 multiply-add chains on every SM (wd_measure_fp64_rate)",
+                "nominal_peak": round(FP64_NOMINAL_GFLOPS / 1e3, 4),
+                "frac_of_nominal": round(d_gflops / FP64_NOMINAL_GFLOPS, 4),
                 "hbm_achieved_gbs": round(d_gbs, 1), "hbm_frac": round(d_gbs / peaks["hbm_gbs"], 4),
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
     else:
@@ -499,6 +530,7 @@ def main():
     roof["algorithmic_flops_per_launch"] = FLOP_PER_SITE * V * nrhs
     roof["avg_launch_ms"] = round(d_ms, 5)
     roof["dslash_gflops"] = round(d_gflops, 2)
+    roof["dslash_hbm_gbs"] = round(d_gbs, 1)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -507,17 +539,131 @@ def main():
             "cg": {"time_to_solution_ms": round(step_ms, 4), "iterations": iters,
                    "reliable_updates": max(r["reliable_updates"] for r in results),
                    "true_rel_resid": max(r["true_rel_resid"] for r in results),
+                   "true_rel_resid_b": max(r["true_rel_resid_b"] for r in results),
                    "operator_applications": n_apply},
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
             "autotuned_tiles": {p: {"site_tile": t[0], "rhs_tile": t[1]} for p, t in tuned.items()},
             "e2e": e2e}
+    if not args.headline_only and nrhs == 1 and world == 1:
+        line["cg"]["variants"] = cg_variants(wd, torch, lat, w, fb, fx, flush, step_ms, args)
+        if args.workload == "c3":
+            lat.close()
+            line["multi_rhs"] = multi_rhs_block(wd, torch, flush, args)
     if args.sweep:
         line["dslash_sweep"] = sweep(wd, torch, flush, stream, args.recon)
-    if not args.no_cpu_baseline and rank == 0:
+    if not args.no_cpu_baseline and not args.headline_only and rank == 0:
         line["cpu_baseline"] = cpu_baseline(w, U, b)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def _median_solve_ms(torch, flush, fn, reps):
+    """Median device time (CUDA events) of fn over reps runs after one warm-up, L2 flushed
+    before each; returns (ms, last result)."""
+    out = fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), out
+
+
+# (name, inner precision, even-odd, inner-precision link compression, stop rule)
+CG_VARIANTS = (("f32", "f32", 0, None, 0), ("f16", "f16", 0, None, 0), ("df32", "df32", 0, None, 0),
+               ("f64_eo", "f64", 1, None, 0), ("f32_eo", "f32", 1, None, 0), ("f16_eo", "f16", 1, None, 0),
+               ("df32_eo", "df32", 1, None, 0), ("f32_recon12_inner", "f32", 0, 12, 0),
+               ("f32_eo_recon12_inner", "f32", 1, 12, 0), ("f16_eo_recon12_inner", "f16", 1, 12, 0),
+               ("f64_system_rule", "f64", 0, None, 1), ("f32_eo_recon12_inner_system_rule", "f32", 1, 12, 1))
+
+
+def cg_variants(wd, torch, lat, w, fb, fx_f64, flush, f64_ms, args):
+    """Every solver variant on the step's lattice and source: time to a true FP64 residual of
+    1e-10 (normal residual; the system rule: |b - D x| / |b|), against the FP64 step."""
+    x64 = lat.unpack(fx_f64)
+    reps = 3
+    out = {"reps": f"median of {reps} after one warm-up, L2 flushed before each",
+           "reference": f"plain FP64 CGNR step, {round(f64_ms, 3)} ms"}
+    for name, inner, eo, rin, rule in CG_VARIANTS:
+        pid = wd.PRECS[inner]
+        if rin:
+            lat.set_link_compression(pid, rin)
+        fx = lat.new_field()
+
+        def solve():
+            fx.zero_()
+            return lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=pid, raise_on_fail=False, precondition=eo,
+                          stop_rule=rule)
+
+        ms, (res, st) = _median_solve_ms(torch, flush, solve, reps)
+        r = res[0]
+        out[name] = {"ms": round(ms, 3), "speedup_vs_f64": round(f64_ms / ms, 3), "iters": r["iters"],
+                     "reliable_updates": r["reliable_updates"], "status": st,
+                     "true_rel_resid": r["true_rel_resid"], "true_rel_resid_b": r["true_rel_resid_b"],
+                     "rel_diff_vs_f64_solution": rel_diff(lat.unpack(fx), x64)}
+        if rin:
+            lat.set_link_compression(pid, args.recon)
+        del fx
+    return out
+
+
+def multi_rhs_block(wd, torch, flush, args):
+    """The 12 spin-colour point sources of the 24^3 x 48 workload: one multi-RHS solve against
+    12 sequential FP64 solves, each to a true FP64 residual of 1e-10."""
+    w = WORKLOADS["c4"]
+    U, B = make_inputs(w, 0)
+    lat = wd.Lattice(w["dims"])
+    lat.set_gauge(U, recon=args.recon)
+    for p in ("f64", "f32"):
+        lat.autotune(wd.PRECS[p], 1)
+        lat.autotune(wd.PRECS[p], 12)
+    fb = lat.pack(B)
+    fbs = [lat.pack(B[k]) for k in range(12)]
+    fys = [lat.new_field() for _ in range(12)]
+    reps = 2
+
+    def seq():
+        res = []
+        for k in range(12):
+            fys[k].zero_()
+            res.append(lat.cg(w["kappa"], fbs[k], fys[k], tol=1e-10)[0][0])
+        return res
+
+    ms_seq, res_seq = _median_solve_ms(torch, flush, seq, reps)
+    Xs = [lat.unpack(f) for f in fys]
+    out = {"workload": "c4: 24x24x24x48 haar links, kappa=0.12, 12 point sources at the origin",
+           "reps": f"median of {reps} after one warm-up",
+           "sequential_f64": {"ms": round(ms_seq, 3), "iters_max": max(r["iters"] for r in res_seq),
+                              "max_true_rel_resid": max(r["true_rel_resid"] for r in res_seq)}}
+    for name, inner, eo, rin in (("multi_rhs_f64", "f64", 0, None), ("multi_rhs_f32", "f32", 0, None),
+                                 ("multi_rhs_f32_eo_recon12_inner", "f32", 1, 12)):
+        pid = wd.PRECS[inner]
+        if rin:
+            lat.set_link_compression(pid, rin)
+        fx = lat.new_field(nrhs=12)
+
+        def solve():
+            fx.zero_()
+            return lat.cg(w["kappa"], fb, fx, tol=1e-10, inner=pid, nrhs=12, raise_on_fail=False, precondition=eo)
+
+        ms, (res, st) = _median_solve_ms(torch, flush, solve, reps)
+        X = lat.unpack(fx, nrhs=12, squeeze=False)
+        out[name] = {"ms": round(ms, 3), "speedup_vs_sequential_f64": round(ms_seq / ms, 3), "status": st,
+                     "iters_max": max(r["iters"] for r in res),
+                     "max_true_rel_resid": max(r["true_rel_resid"] for r in res),
+                     "max_rel_diff_vs_sequential": max(rel_diff(X[k], Xs[k]) for k in range(12))}
+        if rin:
+            lat.set_link_compression(pid, args.recon)
+        del fx
+    lat.close()
+    return out
 
 
 def rel_diff(a, b) -> float:

@@ -152,18 +152,23 @@ wd_status wd_normal_apply(wd_ctx *ctx, double kappa, const void *in, void *out, 
  * fixed once at start-up (a memory pool that owns the rest of the GPU), or a
  * latency-critical loop that must not pay for cudaMalloc/cudaFree, which may
  * synchronise the whole device.  The paper has no counterpart; this is an
- * interface variant of wd_normal_apply.
+ * interface variant of wd_normal_apply, with the same precisions (WD_F64, WD_F32,
+ * WD_F16, WD_DF32) and argument checks (a non-finite kappa is WD_ERR_ARG).
  *
  * The intermediate field D in lives in a fixed file-scope device array of
  * 16 MiB (every GPU that loads the library keeps it until the process exits), so
  * wd_field_bytes(ctx, prec, nrhs) must not exceed 16 MiB: larger requests return
  * WD_ERR_ARG before anything is launched (FP64 fits 16^4 sites with one
- * right-hand side).  The gauge copy of precision prec must already exist
- * (WD_F64 exists after wd_set_gauge; the first wd_apply in WD_F32 or WD_F16
- * creates the others), else WD_ERR_STATE.  The context's device must be current.
+ * right-hand side).  The gauge copy of precision prec must already exist, else
+ * WD_ERR_STATE: wd_set_gauge creates the WD_F64 copy, the first wd_apply in another
+ * precision creates that one, and wd_set_link_compression drops the copy of the
+ * precision it changes (WD_F64 included) until the next wd_apply in it.  The
+ * context's device must be current.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ * The first call on each context looks up the array's device address
+ * (cudaGetSymbolAddress) with the context's device current and keeps it in the
+ * context; it is valid in the CUDA context that was current then, like the
+ * context's other device buffers.  Make that first call before any stream capture.
  * All calls share the array and it keeps the last call's contents; calls whose
  * kernels overlap on the GPU (different streams or host threads) race on it. */
 wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs);
@@ -177,7 +182,8 @@ wd_status wd_normal_apply_noalloc(wd_ctx *ctx, double kappa, const void *in, voi
 wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, int dagger);
 
 /* Solver parameters.
- *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side)
+ *   tol        stop when ||D^dag(b - D x)|| <= tol ||D^dag b|| (per right-hand side;
+ *              see stop_rule)
  *   max_iter   iteration limit
  *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16 / WD_DF32: mixed precision --
  *              the Dslash and the inner iteration in FP32 (or FP16 storage with FP32
@@ -204,9 +210,21 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *              and resumed from its solution with a tighter tolerance (at most three
  *              times) until the recomputed FP64 residual of D x = b on the whole
  *              lattice meets tol; iterations are summed.  Needs even extents; CGNR
- *              only (not with block or normal_eq). */
+ *              only (not with block or normal_eq).
+ *   stop_rule  WD_STOP_NORMAL (default): tol applies to the normal-equation residual,
+ *              ||D^dag(b - D x)|| <= tol ||D^dag b||.  WD_STOP_SYSTEM: tol applies to the
+ *              residual of D x = b itself, ||b - D x|| <= tol ||b|| (the residual the
+ *              paper's listing iterates, section 2.2), which bounds the solution error by
+ *              cond(D) tol.  CGNR iterates the normal residual, so it runs to tol and, while
+ *              the recomputed FP64 ||b - D x|| / ||b|| is above tol, resumes from its own
+ *              solution with the normal tolerance tightened by the observed ratio of the
+ *              two residuals (at most three times; iterations are summed).  With normal_eq
+ *              = 1 the iteration already stops on ||b - D x||.  Not with block CG or the
+ *              batched solver (WD_ERR_ARG). */
 #define WD_PRECOND_NONE 0
 #define WD_PRECOND_EO 1
+#define WD_STOP_NORMAL 0
+#define WD_STOP_SYSTEM 1
 typedef struct wd_cg_params {
     double tol;
     int max_iter;
@@ -217,6 +235,7 @@ typedef struct wd_cg_params {
     int rhs_tile;
     int normal_eq;
     int precondition;
+    int stop_rule;
 } wd_cg_params;
 
 /* Per right-hand side result.  The two residuals are recomputed from the returned x
@@ -271,6 +290,14 @@ wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *
  * and WD_DF32 run each site on two lanes (site_tile / 2 sites per block) and need
  * site_tile >= 32.  Unsupported shapes: WD_ERR_ARG. */
 wd_status wd_set_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int site_tile, int rhs_tile);
+
+/* Measured FP64 arithmetic rate of the current device, in GFLOP/s (2 flop per fused
+ * multiply-add): independent FP64 multiply-add chains on every SM, no memory traffic,
+ * timed with CUDA events on a stream of its own (best of five launches after one
+ * warm-up).  No counterpart in the paper: on GB300 the FP64 Dslash is bound by the
+ * FP64 units, and this is the roof it is reported against.  Synchronises that stream;
+ * changes no device setting.  Errors: WD_ERR_ARG (null), WD_ERR_CUDA. */
+wd_status wd_measure_fp64_rate(double *gflops);
 
 /* Launch-configuration query: number of kernel launches the last wd_* call queued
  * (graph kernel nodes count once per execution). */

@@ -560,6 +560,8 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
         return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: inner_prec must be WD_F32 or WD_F16");
     if ((prm->nrhs > 1) || !(prm->tol > 0)) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: bad nrhs or tol");
     if (prm->normal_eq) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: solves D^dag D only (normal_eq = 0)");
+    if (prm->stop_rule != WD_STOP_NORMAL)
+        return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: stops on the normal residual only");
     const Prec sp = (Prec)prm->inner_prec;
     std::vector<LatDesc> lat(n);
     std::vector<int> tile_lat;

@@ -75,7 +75,11 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (prm->normal_eq != 0 && prm->normal_eq != 1) return fail(c, WD_ERR_ARG, "wd_cg_solve: normal_eq must be 0 or 1");
     if (prm->precondition != WD_PRECOND_NONE && prm->precondition != WD_PRECOND_EO)
         return fail(c, WD_ERR_ARG, "wd_cg_solve: unknown preconditioner");
+    if (prm->stop_rule != WD_STOP_NORMAL && prm->stop_rule != WD_STOP_SYSTEM)
+        return fail(c, WD_ERR_ARG, "wd_cg_solve: unknown stop_rule");
     const bool eo = prm->precondition == WD_PRECOND_EO;
+    // CGNE iterates b - D x itself; CGNR resumes until the recomputed |b - D x| meets tol
+    const bool stop_sys = prm->stop_rule == WD_STOP_SYSTEM && !prm->normal_eq;
     if (eo) {
         if (prm->block || prm->normal_eq)
             return fail(c, WD_ERR_ARG, "wd_cg_solve: even-odd preconditioning is built for plain CGNR");
@@ -85,6 +89,8 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (prm->block) {
         if (prm->inner_prec != WD_F64) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG runs in FP64 only");
         if (prm->normal_eq) return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG solves D^dag D only");
+        if (prm->stop_rule != WD_STOP_NORMAL)
+            return fail(c, WD_ERR_ARG, "wd_cg_solve: block CG stops on the normal residual only");
         return block_cg_solve(c, kappa, b, x, prm, res);
     }
     const Prec inner = (Prec)prm->inner_prec;
@@ -178,6 +184,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     // per-RHS state.  With even-odd preconditioning tol applies to the reduced system,
     // so the solve runs with half of it and is resumed from its own solution, with a
     // tighter reduced tolerance, until the recomputed full-lattice residual meets tol.
+    // With the system-residual rule the same resumption runs until |b - D x| meets tol.
     std::vector<Scalars> h(nrhs);
     const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec);
     void *bin = eo ? f.eo.bfull : f.b, *xin = eo ? f.eo.xfull : f.x;
@@ -188,7 +195,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     std::vector<int> iters(nrhs, 0), reliable(nrhs, 0);
     float ms_total = 0.f;
     long long launches = 0;
-    const int attempts = eo ? 4 : 1;
+    const int attempts = (eo || stop_sys) ? 4 : 1;
     for (int attempt = 0; attempt < attempts; ++attempt) {
         for (int r = 0; r < nrhs; ++r) {
             std::memset(&h[r], 0, sizeof(Scalars));
@@ -230,11 +237,12 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
             iters[r] += h[r].iter;
             reliable[r] += h[r].reliable;
             all_ok &= h[r].status == WD_OK;
-            const double tr = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
+            const double tr = stop_sys ? (h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2))
+                                       : (h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2));
             worst_resid = tr > worst_resid ? tr : worst_resid;
         }
-        if (!eo || !all_ok || worst_resid <= prm->tol || !(worst_resid > 0)) break;
-        tol_run *= 0.5 * prm->tol / worst_resid;
+        if (attempts == 1 || !all_ok || worst_resid <= prm->tol || !(worst_resid > 0)) break;
+        tol_run *= (eo ? 0.5 : 0.7) * prm->tol / worst_resid;
         if (attempt == attempts - 1)
             for (int r = 0; r < nrhs; ++r) h[r].status = WD_ERR_NOT_CONVERGED;
     }

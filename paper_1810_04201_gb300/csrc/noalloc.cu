@@ -11,32 +11,29 @@
 // the last call; the first pass overwrites every byte the second pass reads, so
 // nothing needs clearing.  Calls whose kernels overlap on the GPU (two streams,
 // or two host threads) race on the array.
-#include <mutex>
+#include <cmath>
 #include "dslash.cuh"
 #include "wd_host.h"
 
 using namespace wd;
 
 #define WD_NOALLOC_SCRATCH_BYTES (16u << 20)
-#define WD_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[WD_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device.  In host code the symbol names a
-// host-side stand-in, so the address has to be fetched once per device with that
-// device current.
-static void *g_scratch_addr[WD_NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mu;
-
-static wd_status scratch_address(wd_ctx *c, int dev, void **out) {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+// Device address of g_noalloc_scratch for this context.  In host code the symbol
+// names a host-side stand-in, so the address is looked up with the context's device
+// current, on the first call of each context, and kept in the context beside its
+// other device resources: it is valid in the CUDA context that was current then (the
+// one the wd_ctx's own buffers belong to), and a wd_ctx never outlives that.
+static wd_status scratch_address(wd_ctx *c, void **out) {
+    if (!c->noalloc_scratch) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_scratch_addr[dev] = p;
+        c->noalloc_scratch = p;
     }
-    *out = g_scratch_addr[dev];
+    *out = c->noalloc_scratch;
     return WD_OK;
 }
 
@@ -44,9 +41,10 @@ extern "C" wd_status wd_normal_apply_noalloc(wd_ctx *c, double kappa, const void
                                              int nrhs) {
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
-    if (!in || !out || (int)prec < 0 || (int)prec > 2 || nrhs < 1 || nrhs > WD_MAX_RHS)
+    if (!in || !out || (int)prec < 0 || (int)prec >= kNumPrec || nrhs < 1 || nrhs > WD_MAX_RHS)
         return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: bad argument");
     if (in == out) return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: in and out must be distinct");
+    if (!std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: kappa not finite");
     const size_t need = spinor_bytes((Prec)prec, c->g.Vs) * (size_t)nrhs;
     if (need > WD_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
@@ -59,14 +57,14 @@ extern "C" wd_status wd_normal_apply_noalloc(wd_ctx *c, double kappa, const void
     if (!c->has_gauge) return fail(c, WD_ERR_STATE, "wd_normal_apply_noalloc: no gauge field set");
     if (!c->gauge[prec])
         return fail(c, WD_ERR_STATE,
-                    "wd_normal_apply_noalloc: the gauge copy in this precision does not exist yet; one wd_apply "
-                    "in this precision creates it (and allocates)");
+                    "wd_normal_apply_noalloc: the gauge copy in this precision does not exist (yet, or any more "
+                    "after wd_set_link_compression); one wd_apply in this precision creates it (and allocates)");
     int dev = -1;
     WD_CUDA(c, cudaGetDevice(&dev));
-    if (dev != c->device || dev < 0 || dev >= WD_NOALLOC_MAX_DEVICES)
+    if (dev != c->device)
         return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: the context's device must be the current device");
     void *tmp = nullptr;
-    wd_status s = scratch_address(c, dev, &tmp);
+    wd_status s = scratch_address(c, &tmp);
     if (s != WD_OK) return s;
 
     DslashArgs a{};

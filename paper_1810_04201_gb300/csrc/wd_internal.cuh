@@ -548,6 +548,7 @@ struct wd_ctx {
     std::map<std::string, void *> graphs;              // cached cudaGraphExec_t per solver signature
     std::map<std::string, std::vector<long long>> graph_info;
     std::map<int, wd::DslashTiles> tiles;              // key: prec*64 + nrhs
+    void *noalloc_scratch = nullptr;                   // device address of the allocation-free scratch array
     ~wd_ctx();
 };
 

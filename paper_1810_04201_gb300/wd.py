@@ -28,7 +28,8 @@ MAX_RHS = 16
 class CGParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("nrhs", ctypes.c_int), ("block", ctypes.c_int),
-                ("rhs_tile", ctypes.c_int), ("normal_eq", ctypes.c_int), ("precondition", ctypes.c_int)]
+                ("rhs_tile", ctypes.c_int), ("normal_eq", ctypes.c_int), ("precondition", ctypes.c_int),
+                ("stop_rule", ctypes.c_int)]
 
 
 class CGResult(ctypes.Structure):
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "wd_autotune": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "wd_set_tiles": ([P, I, I, I, I], I),
         "wd_kernel_launches": ([P], ctypes.c_longlong),
+        "wd_measure_fp64_rate": ([ctypes.POINTER(D)], I),
         "wd_status_string": ([I], ctypes.c_char_p),
         "wd_last_error": ([P], ctypes.c_char_p),
     }
@@ -225,14 +227,15 @@ class Lattice:
     # ------------------------------------------------------------------ solvers
     @staticmethod
     def params(tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0, rhs_tile=0, normal_eq=0,
-               precondition=0):
-        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile, normal_eq, precondition)
+               precondition=0, stop_rule=0):
+        return CGParams(tol, max_iter, inner, delta, nrhs, block, rhs_tile, normal_eq, precondition, stop_rule)
 
     def cg(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1, block=0,
-           raise_on_fail=True, normal_eq=0, precondition=0):
+           raise_on_fail=True, normal_eq=0, precondition=0, stop_rule=0):
         """Solve D x = b on device fields (x holds the start vector). Returns the per-RHS results.
-        normal_eq=1 selects CGNE (D D^dag y = b, x = D^dag y); precondition=1 even-odd."""
-        p = self.params(tol, max_iter, inner, delta, nrhs, block, 0, normal_eq, precondition)
+        normal_eq=1 selects CGNE (D D^dag y = b, x = D^dag y); precondition=1 even-odd;
+        stop_rule=1 applies tol to |b - D x| / |b| instead of the normal residual."""
+        p = self.params(tol, max_iter, inner, delta, nrhs, block, 0, normal_eq, precondition, stop_rule)
         res = (CGResult * nrhs)()
         st = self.lib.wd_cg_solve(self.ctx, float(kappa), ctypes.c_void_p(b.data_ptr()),
                                   ctypes.c_void_p(x.data_ptr()), ctypes.byref(p), res)
@@ -241,10 +244,10 @@ class Lattice:
         return [r.as_dict() for r in res], st
 
     def cg_canonical(self, kappa, b, x, tol=1e-10, max_iter=10000, inner=WD_F64, delta=0.0, nrhs=1,
-                     raise_on_fail=True, precondition=0):
+                     raise_on_fail=True, precondition=0, stop_rule=0):
         """End-to-end solve on canonical host arrays (numpy complex128, pinned torch CPU tensors
         allowed) or device tensors; x is overwritten with the solution."""
-        p = self.params(tol, max_iter, inner, delta, nrhs, 0, 0, 0, precondition)
+        p = self.params(tol, max_iter, inner, delta, nrhs, 0, 0, 0, precondition, stop_rule)
         res = (CGResult * nrhs)()
         if isinstance(b, torch.Tensor):
             on_dev = int(b.is_cuda)
@@ -277,6 +280,16 @@ class Lattice:
 
     def set_tiles(self, prec, nrhs, site_tile, rhs_tile):
         self._check(self.lib.wd_set_tiles(self.ctx, prec, nrhs, site_tile, rhs_tile), "wd_set_tiles")
+
+
+def measure_fp64_rate() -> float:
+    """GFLOP/s of independent FP64 multiply-add chains on the current device (wd_measure_fp64_rate)."""
+    lib = load_library()
+    g = ctypes.c_double()
+    st = lib.wd_measure_fp64_rate(ctypes.byref(g))
+    if st != 0:
+        raise WDError(st, "wd_measure_fp64_rate failed")
+    return float(g.value)
 
 
 def device_tag() -> str:
@@ -329,7 +342,7 @@ def cg_batched(lattices, kappas, bs, xs, tol=1e-10, max_iter=10000, inner=WD_F32
     ks = (ctypes.c_double * n)(*[float(k) for k in kappas])
     bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
     xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
-    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0, 0, 0)
+    p = CGParams(tol, max_iter, inner, delta, 1, 0, 0, 0, 0, 0)
     res = (CGResult * n)()
     st = lib.wd_cg_solve_batched(ctxs, ks, bp, xp, n, ctypes.byref(p), res)
     return [r.as_dict() for r in res], st

@@ -19,7 +19,7 @@ from paper_1810_04201_gb300 import gen
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2e-6}
+TOL = {0: 1e-13, 1: 2e-6, 2: 4e-3, 3: 1e-13}
 
 
 @pytest.fixture(scope="module")
@@ -30,8 +30,11 @@ def wd():
     return _wd
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_noalloc_matches_normal_apply_twice(wd, prec):
+@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_noalloc_matches_normal_apply_twice(wd, prec, nrhs):
+    """Every precision's field layout (the FP16 per-site scale block included) and the
+    stride between right-hand sides inside the fixed array."""
     import torch
     dims, kappa = (8, 8, 6, 10), 0.12
     U = gen.haar_links(dims, seed=31)
@@ -41,17 +44,20 @@ def test_noalloc_matches_normal_apply_twice(wd, prec):
         # creates the lower-precision gauge copy (this call may allocate)
         lat.apply(kappa, lat.new_field(prec), lat.new_field(prec), prec)
     for call, seed in enumerate((41, 42)):
-        psi = gen.gaussian_source(dims, seed=seed)
-        f = lat.pack(psi, prec)
-        ref = lat.new_field(prec)
-        got = lat.new_field(prec)
-        lat.normal_apply(kappa, f, ref, prec)
-        lat.normal_apply_noalloc(kappa, f, got, prec)
+        psi = np.stack([gen.gaussian_source(dims, seed=seed + 10 * k) for k in range(nrhs)])
+        f = lat.pack(psi if nrhs > 1 else psi[0], prec)
+        ref = lat.new_field(prec, nrhs=nrhs)
+        got = lat.new_field(prec, nrhs=nrhs)
+        lat.normal_apply(kappa, f, ref, prec, nrhs=nrhs)
+        lat.normal_apply_noalloc(kappa, f, got, prec, nrhs=nrhs)
         assert lat.launches == 2
         torch.cuda.synchronize()
-        a, b = lat.unpack(got, prec), lat.unpack(ref, prec)
-        assert oracle.rel_err(a, b) < TOL[prec], (call, oracle.rel_err(a, b))
-        assert oracle.rel_err(a, oracle.apply_normal(U, psi, kappa, dims)) < TOL[prec] * 4
+        a = np.reshape(lat.unpack(got, prec, nrhs=nrhs), psi.shape)
+        b = np.reshape(lat.unpack(ref, prec, nrhs=nrhs), psi.shape)
+        for k in range(nrhs):
+            assert oracle.rel_err(a[k], b[k]) < TOL[prec], (call, k, oracle.rel_err(a[k], b[k]))
+            want = oracle.apply_normal(U, psi[k], kappa, dims)
+            assert oracle.rel_err(a[k], want) < TOL[prec] * 4, (call, k)
 
 
 def test_noalloc_rejects_oversize_and_missing_gauge_copy(wd):
@@ -63,6 +69,9 @@ def test_noalloc_rejects_oversize_and_missing_gauge_copy(wd):
         lat.normal_apply_noalloc(0.12, f2, lat.new_field(0, nrhs=2), 0, nrhs=2)
     assert e.value.status == 1 and "16777216" in str(e.value)
     f1 = lat.new_field(2)
+    with pytest.raises(wd.WDError) as e:  # a non-finite kappa, checked before anything runs
+        lat.normal_apply_noalloc(float("nan"), lat.new_field(0), lat.new_field(0), 0)
+    assert e.value.status == 1 and "kappa" in str(e.value)
     with pytest.raises(wd.WDError) as e:  # no FP16 gauge copy yet
         lat.normal_apply_noalloc(0.12, f1, lat.new_field(2), 2)
     assert e.value.status == 8
