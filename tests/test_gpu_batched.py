@@ -154,3 +154,42 @@ def test_batched_iteration_limit_reports_residual_of_x(wd):
         assert rn > 1e-10
         assert res[i]["true_rel_resid"] == pytest.approx(rn, rel=1e-6), i
         assert res[i]["true_rel_resid_b"] == pytest.approx(rb, rel=1e-6), i
+
+
+@pytest.mark.parametrize("rin", [18, 12])
+def test_batched_full_c5_workload(wd, rin):
+    """The 64-lattice uneven workload the bench times (shapes from {8^4, 8^3x16, 12^4, 12^3x24,
+    16^4}, kappa in [0.10, 0.125], per-lattice seeds 100 + i; 1.86 M sites, many tiles per
+    lattice), in its launch configuration: FP32 inner iterations, whole FP64 links, inner links
+    whole or recon-12.  Every lattice's solution is checked through the oracle's operator (the
+    residuals b - D x and D^dag (b - D x) recomputed on the host, which must be the ones the
+    library reports and meet the tolerance), and two of them, a 16^4 and a 12^3 x 24, element by
+    element against the oracle's own CG solution."""
+    shapes, kappas, seeds = gen.batch_workload(64)
+    lats, bs, xs, inputs = [], [], [], []
+    for dims, seed in zip(shapes, seeds):
+        U = gen.haar_links(dims, seed)
+        b = gen.gaussian_source(dims, seed)
+        lat = wd.Lattice(dims)
+        lat.set_gauge(U)
+        if rin != 18:
+            lat.set_link_compression(1, rin)
+        lats.append(lat)
+        bs.append(lat.pack(b))
+        xs.append(lat.new_field())
+        inputs.append((U, b))
+    assert sum(l.V for l in lats) > 1_500_000 and {(16, 16, 16, 16), (12, 12, 12, 24)} <= set(shapes)
+    res, st = wd.cg_batched(lats, kappas, bs, xs, tol=1e-10, inner=1)
+    assert st == 0, [r for r in res if r["status"] != 0][:3]
+    for i, (lat, (U, b)) in enumerate(zip(lats, inputs)):
+        x = lat.unpack(xs[i])
+        rb, rn = oracle_residuals(U, b, x, kappas[i], lat.dims)
+        assert res[i]["status"] == 0 and rn <= 1.01e-10, (i, rn)
+        assert res[i]["true_rel_resid"] == pytest.approx(rn, rel=1e-3), i
+        assert res[i]["true_rel_resid_b"] == pytest.approx(rb, rel=1e-3), i
+    for dims in ((16, 16, 16, 16), (12, 12, 12, 24)):
+        i = shapes.index(dims)
+        U, b = inputs[i]
+        x_ref, _ = oracle.cgnr(U, b, kappas[i], dims, tol=1e-13)
+        assert oracle.rel_err(lats[i].unpack(xs[i]), x_ref) < 1e-9, (i, dims)
+    assert len({r["iters"] for r in res}) > 1
