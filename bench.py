@@ -364,6 +364,8 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="with --dslash-only: autotune the launch shape first")
+    ap.add_argument("--staged", default=None, metavar="ROWS[,STAGES]",
+                    help="with --dslash-only: the kernel with neighbour spinors staged through shared memory")
     ap.add_argument("--compare", action="store_true",
                     help="c3: FP64 vs FP32 vs FP16-storage solves; c4: 12 sequential FP64 solves vs multi-RHS "
                          "and block CG; c5: batched persistent solve vs one-at-a-time FP64 solves")
@@ -407,6 +409,8 @@ def main():
         lat.set_link_compression(wd.PRECS[inner], args.recon_inner)
     # the autotuner picks the thread-block shape of the Dslash for this lattice
     tuned = {p: lat.autotune(wd.PRECS[p], nrhs) for p in sorted({"f64", inner})}
+    # and the solver autotuner the launch shape of the fused CG kernels, as the solver runs them
+    tuned_cg = {p: lat.autotune_cg(wd.PRECS[p], nrhs) for p in sorted({"f64", inner})}
     fb = lat.pack(b)
     fx = lat.new_field(nrhs=nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -543,6 +547,7 @@ def main():
                    "operator_applications": n_apply},
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
             "autotuned_tiles": {p: {"site_tile": t[0], "rhs_tile": t[1]} for p, t in tuned.items()},
+            "autotuned_cg_tiles": {p: {"site_tile": t[0], "rhs_tile": t[1]} for p, t in tuned_cg.items()},
             "e2e": e2e}
     if not args.headline_only and nrhs == 1 and world == 1:
         line["cg"]["variants"] = cg_variants(wd, torch, lat, w, fb, fx, flush, step_ms, args)
@@ -588,6 +593,8 @@ def cg_variants(wd, torch, lat, w, fb, fx_f64, flush, f64_ms, args):
     """Every solver variant on the step's lattice and source: time to a true FP64 residual of
     1e-10 (normal residual; the system rule: |b - D x| / |b|), against the FP64 step."""
     x64 = lat.unpack(fx_f64)
+    for p in sorted({v[1] for v in CG_VARIANTS} - {"f64"}):
+        lat.autotune_cg(wd.PRECS[p], 1)
     reps = 3
     out = {"reps": f"median of {reps} after one warm-up, L2 flushed before each",
            "reference": f"plain FP64 CGNR step, {round(f64_ms, 3)} ms"}
@@ -622,8 +629,9 @@ def multi_rhs_block(wd, torch, flush, args):
     lat = wd.Lattice(w["dims"])
     lat.set_gauge(U, recon=args.recon)
     for p in ("f64", "f32"):
-        lat.autotune(wd.PRECS[p], 1)
-        lat.autotune(wd.PRECS[p], 12)
+        for n in (1, 12):
+            lat.autotune(wd.PRECS[p], n)
+            lat.autotune_cg(wd.PRECS[p], n)
     fb = lat.pack(B)
     fbs = [lat.pack(B[k]) for k in range(12)]
     fys = [lat.new_field() for _ in range(12)]
@@ -832,6 +840,10 @@ def dslash_only(args):
     b = gen.gaussian_source(dims, 4, nrhs=args.nrhs)
     pid = PREC_ID[args.prec]
     tiles = lat.autotune(pid, args.nrhs) if args.autotune else None
+    if args.staged:
+        parts = [int(v) for v in args.staged.split(",")]
+        lat.set_staging(pid, parts[0], parts[1] if len(parts) > 1 else 2)
+        tiles = {"staged_rows": parts[0], "stages": parts[1] if len(parts) > 1 else 2}
     fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
     fo = lat.new_field(pid, args.nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -849,6 +861,8 @@ def dslash_only(args):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = statistics.mean(ts)
+    if args.staged and lat.staging_error():
+        raise RuntimeError("a wait of the staged kernel ran out")
     V = lat.V
     nb = V * (args.nrhs * 2 * SPINOR_BYTES[args.prec] + LINK_BYTES[(args.prec, args.recon)])
     print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs, "tiles": tiles,

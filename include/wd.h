@@ -285,11 +285,101 @@ wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kappas, const v
  * the fastest for later calls.  Writes the choice to *site_tile and *rhs_tile
  * (either may be NULL).  Uses context-owned scratch fields; synchronises the stream. */
 wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
+/* Autotuner of the solvers: times the same candidates for the fused CG kernels (the
+ * Dslash with the CG epilogues and reductions) as wd_cg_solve runs them -- ten iterations
+ * of the device-resident loop in inner precision prec (WD_F64: the plain FP64 solver) on a
+ * non-zero right-hand side, L2 flushed before each timed solve -- and keeps the fastest
+ * for the solvers of this precision and nrhs (wd_cg_solve, wd_cg_solve_canonical); the
+ * plain operators keep wd_autotune's choice.  Uses and frees context scratch (256 MB for
+ * the flush); synchronises the stream. */
+wd_status wd_autotune_cg(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
+/* Neighbour staging for the plain FP32 and FP16 operators (the paper's on-chip buffers
+ * that feed the stencil pipeline, sections 6.3-6.4): with rows > 0, wd_apply,
+ * wd_apply_dagger and wd_normal_apply in precision prec run a persistent kernel whose
+ * blocks take tiles of `rows` whole x-rows (rows * Lx sites, rows dividing Ly, at most 256
+ * sites) and fetch each tile's neighbour spinors -- the tile, the two adjacent rows, and the
+ * same sites one plane and one slice away in each direction, seven contiguous ranges per
+ * field array -- into shared memory with 1-D bulk copies completed on an mbarrier, `stages`
+ * (2 to 4) tiles in flight per block; links are read directly.  rows = 0 returns to the
+ * direct-load kernel (the default; the solvers always use it, since their epilogues are
+ * fused into it).  FP16 needs Lx a multiple of 4.  Full lattices only (no split or
+ * checkerboard).  Unsupported shapes: WD_ERR_ARG.  No counterpart in the paper beyond the
+ * buffers it mirrors. */
+wd_status wd_set_staging(wd_ctx *ctx, wd_prec prec, int rows, int stages);
+/* The staged kernel bounds its waits; one that ran out since the last call sets *err to 1
+ * (and that launch's output is incomplete).  Synchronises the stream and clears the word. */
+wd_status wd_staging_error(wd_ctx *ctx, unsigned *err);
+
 /* Fix the tile choice by hand: site_tile in {16, 32, 64, 128, 256} threads,
  * 1 <= rhs_tile <= nrhs, site_tile * rhs_tile <= 256 and a multiple of 32.  WD_F64
  * and WD_DF32 run each site on two lanes (site_tile / 2 sites per block) and need
  * site_tile >= 32.  Unsupported shapes: WD_ERR_ARG. */
 wd_status wd_set_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int site_tile, int rhs_tile);
+
+/* ---- Domain decomposition along t (section 2.3: the lattice is divided into
+ * sub-lattices, one per process, each holding copies of its neighbours' boundary sites,
+ * and the scalar products of CG are summed over all of them; section 8: multi-node
+ * systems).  Rank k of nranks owns the global t-slices [k T / nranks, (k + 1) T / nranks).
+ *
+ * A split context is the sub-lattice of one rank: Lx x Ly x Lz x (T / nranks) sites,
+ * T divisible by nranks, at least one slice each.  Its links and fields use the ordinary
+ * layouts of that sub-lattice (wd_set_gauge takes the 4 x V_local x 9 links U_mu(n) of the
+ * rank's own sites, the t links of its last slice included; wd_pack / wd_unpack as usual).
+ * Its Dslash (WD_F64 or WD_F32, any link compression) is two calls:
+ *   wd_apply_interior  every hop whose neighbour is local, with the xpay: out = in - kappa
+ *                      (hops); the t hops that leave the sub-lattice are left out;
+ *   wd_apply_faces     adds -kappa (the two t hops across the faces) at the first and
+ *                      the last slice, from the faces the neighbours sent.
+ * wd_face_pack writes the two faces this rank sends, projected half spinors (6 complex
+ * numbers per face site, 96 bytes in FP64, 48 in FP32, face site f = x + Lx (y + Ly z)):
+ *   to_prev  for rank k - 1 (mod nranks): (1 + s gamma_t) in on the first slice, upper half;
+ *   to_next  for rank k + 1 (mod nranks): U_t(n)^dag times the upper half of
+ *            (1 - s gamma_t) in on the last slice,
+ * with s = -1 for D and +1 for D^dag (dagger).  from_prev of rank k is to_next of rank k - 1,
+ * from_next is to_prev of rank k + 1.  With antiperiodic_t the receiver applies the sign of
+ * the global boundary (ranks 0 and nranks - 1).  The interior launch does not read the
+ * faces, so it can overlap their exchange.  The other operators and solvers refuse split
+ * contexts (WD_ERR_STATE). */
+wd_status wd_create_split(wd_ctx **ctx, const int global_dims[4], int nranks, int rank, int antiperiodic_t,
+                          void *stream);
+/* Bytes of one face buffer (nrhs right-hand sides; 0 when ctx is not split or prec is not
+ * WD_F64 / WD_F32). */
+size_t wd_face_bytes(const wd_ctx *ctx, wd_prec prec, int nrhs);
+wd_status wd_face_pack(wd_ctx *ctx, const void *in, void *to_prev, void *to_next, wd_prec prec, int nrhs, int dagger);
+wd_status wd_apply_interior(wd_ctx *ctx, double kappa, const void *in, void *out, wd_prec prec, int nrhs, int dagger);
+wd_status wd_apply_faces(wd_ctx *ctx, double kappa, const void *from_prev, const void *from_next, void *out,
+                         wd_prec prec, int nrhs, int dagger);
+
+/* Communication with the processes that hold the other sub-lattices of a split lattice.
+ *   exchange   send send_prev (to_prev of this process's first sub-lattice) to the process
+ *              holding the previous rank and receive its to_next into recv_prev; send
+ *              send_next (to_next of the last sub-lattice) to the process holding the
+ *              next rank and receive its to_prev into recv_next.  Device buffers of `bytes`
+ *              bytes; stream is the cudaStream_t the solver works on: the sends may start
+ *              after the work queued there, and on return the receive buffers must be
+ *              complete in that stream's order.  Returns 0 on success.
+ *   allreduce  replace vals[0..n-1] (host memory) by their sums over all processes;
+ *              returns 0 on success. */
+typedef struct wd_comm {
+    void *user;
+    int (*exchange)(void *user, const void *send_prev, void *recv_prev, const void *send_next, void *recv_next,
+                    size_t bytes, void *stream);
+    int (*allreduce)(void *user, double *vals, int n);
+} wd_comm;
+
+/* CGNR (section 2.2) on a lattice split along t: ctxs[0..n-1] are the sub-lattices this
+ * process holds, consecutive ranks on one device (all of them when n = nranks, and then
+ * comm may be NULL); b[i], x[i] their WD_F64 fields (x: start vector in, solution out).
+ * Faces between local sub-lattices are exchanged by device copies on a side stream while
+ * the interior launches run; faces to other processes and every scalar product go through
+ * comm.  Each iteration sums |D p|^2 and |r|^2 over all sub-lattices, and the host takes
+ * alpha, beta and the stopping test (the division of labour of the paper's section 5).
+ * params: plain FP64 (inner_prec WD_F64), nrhs 1, no block, CGNE, preconditioner or
+ * system stopping rule (WD_ERR_ARG otherwise); tol applies to the normal residual.
+ * *result (one, for the whole lattice) holds the residuals of the returned x recomputed
+ * on the whole lattice; the work runs on ctxs[0]'s stream and the call waits for it. */
+wd_status wd_cg_solve_split(wd_ctx *const *ctxs, int n, double kappa, const void *const *b, void *const *x,
+                            const wd_cg_params *params, wd_cg_result *result, const wd_comm *comm);
 
 /* Measured FP64 arithmetic rate of the current device, in GFLOP/s (2 flop per fused
  * multiply-add): independent FP64 multiply-add chains on every SM, no memory traffic,

@@ -31,8 +31,7 @@ wd_status ws_get(wd_ctx *c, const std::string &name, size_t bytes, void **out) {
         cudaFree(it->second);
         c->ws.erase(it);
         // graphs may hold the old pointer
-        for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
-        c->graphs.clear();
+        graph_clear(c);
     }
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -132,6 +131,49 @@ wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes) {
     return WD_OK;
 }
 
+void *graph_get(wd_ctx *c, const std::string &key) {
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) return nullptr;
+    c->graph_used[key] = ++c->graph_tick;
+    return it->second;
+}
+
+void graph_put(wd_ctx *c, const std::string &key, void *exec, const std::vector<long long> &info) {
+    while (c->graphs.size() >= kMaxGraphs) {
+        auto lru = c->graph_used.begin();
+        for (auto it = c->graph_used.begin(); it != c->graph_used.end(); ++it)
+            if (it->second < lru->second) lru = it;
+        cudaGraphExecDestroy((cudaGraphExec_t)c->graphs[lru->first]);
+        c->graphs.erase(lru->first);
+        c->graph_info.erase(lru->first);
+        c->graph_used.erase(lru);
+    }
+    c->graphs[key] = exec;
+    c->graph_info[key] = info;
+    c->graph_used[key] = ++c->graph_tick;
+}
+
+void graph_clear(wd_ctx *c) {
+    for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
+    c->graphs.clear();
+    c->graph_info.clear();
+    c->graph_used.clear();
+}
+
+DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs) {
+    auto it = c->cg_tiles.find(p * 64 + nrhs);
+    return it != c->cg_tiles.end() ? it->second : tiles_for(c, p, nrhs);
+}
+
+void ws_release(wd_ctx *c, const std::string &name) {
+    auto it = c->ws.find(name);
+    if (it == c->ws.end()) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(it->second);
+    c->ws.erase(it);
+    c->ws_size.erase(name);
+}
+
 DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs) {
     auto it = c->tiles.find(p * 64 + nrhs);
     if (it != c->tiles.end()) return it->second;
@@ -197,6 +239,7 @@ wd_status wd_create(wd_ctx **out, const int dims[4], int antiperiodic_t, void *s
     c->g.antiperiodic = antiperiodic_t ? 1 : 0;
     c->g.eo_parity = -1;
     c->g.dbg = nullptr;
+    c->g.split_t = 0;
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
@@ -249,8 +292,7 @@ wd_status wd_set_gauge(wd_ctx *c, const double *U, int on_device, int recon) {
     for (int p = 0; p < kNumPrec; ++p) c->recon_p[p] = 0;
     c->has_gauge = false;
     // graphs bake gauge pointers in
-    for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
-    c->graphs.clear();
+    graph_clear(c);
     if (recon == 8) {
         wd_status s = check_recon8(c, "wd_set_gauge");
         if (s != WD_OK) return s;
@@ -293,8 +335,7 @@ wd_status wd_set_link_compression(wd_ctx *c, wd_prec prec, int recon) {
     if (c->gauge_eo[prec]) cudaFree(c->gauge_eo[prec]);
     c->gauge[prec] = c->gauge_eo[prec] = nullptr;
     c->recon_p[prec] = recon;
-    for (auto &g : c->graphs) cudaGraphExecDestroy((cudaGraphExec_t)g.second);
-    c->graphs.clear();
+    graph_clear(c);
     return WD_OK;
 }
 
@@ -376,6 +417,9 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
         return fail(c, WD_ERR_ARG, std::string(who) + ": bad argument");
     if (in == out) return fail(c, WD_ERR_ARG, std::string(who) + ": in and out must be distinct");
     if (!std::isfinite(kappa)) return fail(c, WD_ERR_ARG, std::string(who) + ": kappa not finite");
+    if (c->split)
+        return fail(c, WD_ERR_STATE, std::string(who) + ": a split sub-lattice needs its faces "
+                                                      "(wd_apply_interior and wd_apply_faces)");
     const void *gauge;
     wd_status s = gauge_get(c, (Prec)prec, &gauge);
     if (s != WD_OK) return s;
@@ -388,7 +432,15 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
     a.gauge_dir = gauge_dir_bytes(c, (Prec)prec);
     a.kappa = kappa;
     a.nrhs = nrhs;
-    WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, tiles_for(c, (Prec)prec, nrhs), c->stream));
+    if (c->staged_rows[prec]) {
+        void *err;
+        if ((s = ws_get(c, "staged_err", sizeof(unsigned), &err)) != WD_OK) return s;
+        WD_CUDA(c, launch_apply_staged(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, c->staged_rows[prec],
+                                       c->staged_stages[prec], static_cast<unsigned *>(err), c->stream));
+    } else {
+        WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, tiles_for(c, (Prec)prec, nrhs),
+                                c->stream));
+    }
     c->launches += 1;
     return WD_OK;
 }
@@ -410,6 +462,7 @@ wd_status wd_normal_apply(wd_ctx *c, double kappa, const void *in, void *out, wd
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (bad_prec(prec) || nrhs < 1 || nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_normal_apply: bad argument");
+    if (c->split) return fail(c, WD_ERR_STATE, "wd_normal_apply: not on a split sub-lattice");
     void *tmp;
     wd_status s = ws_get(c, "normal_tmp", spinor_bytes((Prec)prec, c->g.Vs) * nrhs, &tmp);
     if (s != WD_OK) return s;

@@ -571,6 +571,7 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
         if (!c || !b[i] || !x[i] || !std::isfinite(kappas[i]))
             return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: null context, field or bad kappa");
         if (c->device != c0->device) return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: contexts on different devices");
+        if (c->split) return fail(c0, WD_ERR_STATE, "wd_cg_solve_batched: a split sub-lattice (use wd_cg_solve_split)");
         if (link_recon(c, F64) != link_recon(c0, F64) || link_recon(c, sp) != link_recon(c0, sp))
             return fail(c0, WD_ERR_ARG, "wd_cg_solve_batched: every context needs the same link compressions");
         wd_status s;
@@ -656,17 +657,14 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     char key[160];
     snprintf(key, sizeof key, "batch|%d|%d,%d|%d|%d|%d|%d|%p|%p", (int)sp, r64, rin, n, ntiles, prm->max_iter,
              a.stall_test, d_part, d_lat);
-    cudaGraphExec_t exec;
-    auto it = c0->graphs.find(key);
-    if (it != c0->graphs.end()) {
-        exec = (cudaGraphExec_t)it->second;
-    } else {
+    cudaGraphExec_t exec = (cudaGraphExec_t)graph_get(c0, key);
+    if (!exec) {
         const cudaError_t e = with_recon_pair(r64, rin, [&](auto ra, auto rb) {
             constexpr int R = decltype(ra)::value, RI = decltype(rb)::value;
             return sp == F32 ? build_batched<F32, R, RI>(a, &exec) : build_batched<F16, R, RI>(a, &exec);
         });
         if (e != cudaSuccess) return cuda_fail(c0, e, "building the batched persistent CG graph");
-        c0->graphs[key] = exec;
+        graph_put(c0, key, exec, {});
     }
     EventPair ev;
     WD_CUDA(c0, ev.create());

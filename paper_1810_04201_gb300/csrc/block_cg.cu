@@ -356,11 +356,8 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
     const DslashTiles t64 = tiles_for(c, F64, k);
     char key[200];
     snprintf(key, sizeof key, "bcg|%d|%d|%a|%d,%d", k, link_recon(c, F64), kappa, t64.site_tile, t64.rhs_tile);
-    cudaGraphExec_t exec;
-    auto it = c->graphs.find(key);
-    if (it != c->graphs.end()) {
-        exec = (cudaGraphExec_t)it->second;
-    } else {
+    cudaGraphExec_t exec = (cudaGraphExec_t)graph_get(c, key);
+    if (!exec) {
         cudaGraph_t graph;
         WD_CUDA(c, cudaGraphCreate(&graph, 0));
         cudaGraphConditionalHandle hw = 0;
@@ -379,9 +376,8 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(c, e, "building the block-CG graph");
-        c->graphs[key] = exec;
-        c->graph_info[key] = {(long long)plan.setup.size(), (long long)plan.pre.size(), 0,
-                              (long long)plan.fin.size()};
+        graph_put(c, key, exec, {(long long)plan.setup.size(), (long long)plan.pre.size(), 0,
+                                 (long long)plan.fin.size()});
         WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 256, c->stream));
     }
 

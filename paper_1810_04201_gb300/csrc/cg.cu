@@ -58,6 +58,17 @@ static cudaError_t run_host_loop(wd_ctx *c, const Plan &plan, const Fields &f, i
 wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm,
                          wd_cg_result *res);
 
+// A deterministic non-zero FP64 field (values in [-1, 1) from a hash of the index), the
+// right-hand side of the solver autotuner.
+__global__ void k_fill_hash(double *p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 31)) * 0xD6E8FEB86659FD93ull;
+        z ^= z >> 32;
+        p[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+    }
+}
+
 }  // namespace wd
 
 extern "C" {
@@ -67,6 +78,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (!b || !x || !prm || !res) return fail(c, WD_ERR_ARG, "wd_cg_solve: null argument");
+    if (c->split) return fail(c, WD_ERR_STATE, "wd_cg_solve: a split sub-lattice (use wd_cg_solve_split)");
     const int nrhs = prm->nrhs < 1 ? 1 : prm->nrhs;
     if (nrhs > WD_MAX_RHS) return fail(c, WD_ERR_ARG, "wd_cg_solve: nrhs above WD_MAX_RHS");
     if (prm->inner_prec < 0 || prm->inner_prec >= kNumPrec) return fail(c, WD_ERR_ARG, "wd_cg_solve: bad inner_prec");
@@ -151,7 +163,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (rin != r64 && r64 != 18)
         return fail(c, WD_ERR_ARG, "wd_cg_solve: with compressed FP64 links the inner precision needs the same "
                                    "compression (see wd_set_link_compression)");
-    SolverPlan pl{r64, rin, kappa, nrhs, inner, tiles_for(c, F64, nrhs), tiles_for(c, inner, nrhs),
+    SolverPlan pl{r64, rin, kappa, nrhs, inner, cg_tiles_for(c, F64, nrhs), cg_tiles_for(c, inner, nrhs),
                   prm->normal_eq ? 1 : 0, eo ? 1 : 0};
     char key[256];
     snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, r64, rin, kappa, pl.t64.site_tile,
@@ -166,18 +178,15 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         });
         WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 64, c->stream));
     } else {
-        auto it = c->graphs.find(key);
-        if (it == c->graphs.end()) {
+        exec = (cudaGraphExec_t)graph_get(c, key);
+        if (!exec) {
             std::vector<long long> counts;
             cudaError_t e = with_recon_pair(r64, rin, [&](auto ra, auto rb) {
                 return build_for<decltype(ra)::value, decltype(rb)::value>(c, pl, f, g64, gin, &exec, counts);
             });
             if (e != cudaSuccess) return cuda_fail(c, e, "building the CG graph");
-            c->graphs[key] = exec;
-            c->graph_info[key] = counts;
+            graph_put(c, key, exec, counts);
             WD_CUDA(c, cudaMemsetAsync(f.counter, 0, 256, c->stream));
-        } else {
-            exec = (cudaGraphExec_t)it->second;
         }
     }
 
@@ -284,6 +293,73 @@ wd_status wd_cg_solve_canonical(wd_ctx *c, double kappa, const double *b_canon, 
     if ((s = wd_unpack(c, xf, WD_F64, nrhs, x_canon, on_device)) != WD_OK) return s;
     c->launches = l + 4;
     return sol;
+}
+
+// Solver autotuner: the launch shape of the fused CG kernels is timed as the solver runs
+// them, a fixed number of iterations of the device-resident loop on a non-zero right-hand
+// side, with L2 flushed before each timed solve (the candidates as in wd_autotune).
+wd_status wd_autotune_cg(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile) {
+    wd::NvtxRange nvtx_("wd_autotune_cg");
+    if (!c) return WD_ERR_ARG;
+    c->launches = 0;
+    if ((int)prec < 0 || (int)prec >= kNumPrec || nrhs < 1 || nrhs > WD_MAX_RHS)
+        return fail(c, WD_ERR_ARG, "wd_autotune_cg: bad argument");
+    if (c->split) return fail(c, WD_ERR_STATE, "wd_autotune_cg: not on a split sub-lattice");
+    if (!c->has_gauge) return fail(c, WD_ERR_STATE, "wd_autotune_cg: no gauge field set");
+    const size_t fb = spinor_bytes(F64, c->g.Vs) * (size_t)nrhs;
+    const size_t flush_bytes = (size_t)256 << 20;  // twice the L2 of a GB300
+    void *b, *x, *flush;
+    wd_status s;
+    if ((s = ws_get(c, "tunecg_b", fb, &b)) != WD_OK) return s;
+    if ((s = ws_get(c, "tunecg_x", fb, &x)) != WD_OK) return s;
+    if ((s = ws_get(c, "tunecg_flush", flush_bytes, &flush)) != WD_OK) return s;
+    k_fill_hash<<<1024, 256, 0, c->stream>>>(static_cast<double *>(b), fb / sizeof(double));
+    WD_CUDA(c, cudaGetLastError());
+    wd_cg_params prm{};
+    prm.tol = 1e-20;  // never met: every candidate runs max_iter iterations
+    prm.max_iter = 10;
+    prm.inner_prec = prec;
+    prm.nrhs = nrhs;
+    std::vector<wd_cg_result> res(nrhs);
+    const int key = (int)prec * 64 + nrhs;
+    const int sts[] = {16, 32, 64, 128, 256};
+    const int rts[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    double best = 1e30;
+    DslashTiles bt = cg_tiles_for(c, (Prec)prec, nrhs);
+    long long launches = 1;
+    for (int st : sts)
+        for (int rt : rts) {
+            if (rt > nrhs || st * rt > 256 || (st * rt) % 32 != 0) continue;
+            if (threads_per_site((Prec)prec) > 1 && st % 32 != 0) continue;
+            DslashTiles t;
+            t.site_tile = st;
+            t.rhs_tile = rt;
+            c->cg_tiles[key] = t;
+            double secs = 0.0;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run builds and uploads the graph
+                WD_CUDA(c, cudaMemsetAsync(x, 0, fb, c->stream));
+                WD_CUDA(c, cudaMemsetAsync(flush, rep, flush_bytes, c->stream));
+                s = wd_cg_solve(c, 0.12, b, x, &prm, res.data());
+                if (s != WD_OK && s != WD_ERR_NOT_CONVERGED) {
+                    c->cg_tiles[key] = bt;
+                    return s;
+                }
+                launches += c->launches;
+                secs = res[0].seconds;
+            }
+            if (secs < best) {
+                best = secs;
+                bt = t;
+            }
+        }
+    c->cg_tiles[key] = bt;
+    ws_release(c, "tunecg_flush");
+    ws_release(c, "tunecg_b");
+    ws_release(c, "tunecg_x");
+    c->launches = launches;
+    if (site_tile) *site_tile = bt.site_tile;
+    if (rhs_tile) *rhs_tile = bt.rhs_tile;
+    return WD_OK;
 }
 
 }  // extern "C"

@@ -26,10 +26,10 @@ __device__ __forceinline__ bool reduce_finish(const DslashArgs &a, double (&v)[N
     __shared__ double smem[WD_MAX_RHS * 8 * NV];
     __shared__ double tot[WD_MAX_RHS * NV];
     block_reduce_rows<NV>(v, smem);
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int r = tile_y() * blockDim.y + threadIdx.y;
     if (threadIdx.x == 0 && r < a.nrhs)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) a.partial[((size_t)r * NV + k) * gridDim.x + blockIdx.x] = v[k];
+        for (int k = 0; k < NV; ++k) a.partial[((size_t)r * NV + k) * gridDim.x + tile_x()] = v[k];
     const bool last = last_block(a.counter);
     if (last) {
         sum_partials<NV>(a.partial, gridDim.x, a.nrhs, tot);

@@ -91,6 +91,11 @@ template <int P> struct HasScale { static constexpr bool value = false; };
 template <> struct HasScale<F16> { static constexpr bool value = true; };
 
 // w = U h (forward) or U^dag h (backward), two colour vectors; optional sign flip
+template <class R> __device__ __forceinline__ void zero6(C<R> (&w)[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = C<R>{R(0), R(0)};
+}
+
 template <bool ADJ, class R>
 __device__ __forceinline__ void su3_mult(const C<R> (&u)[9], const C<R> (&h)[6], C<R> (&w)[6], bool flip) {
 #pragma unroll
@@ -124,6 +129,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
         project<MU, SF>(p, h);
         LinkIO<P, RECON>::load(gdir, g.Vs, s, u);
         su3_mult<false>(u, h, w, MU == 3 && g.antiperiodic && c == L - 1);
+        if (MU == 3 && g.split_t && c == L - 1) zero6(w);  // the neighbour lives on the next sub-lattice
         accumulate<MU, SF>(acc, w);
     }
     {
@@ -133,6 +139,7 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const void *in, const cha
         project<MU, -SF>(p, h);
         LinkIO<P, RECON>::load(gdir, g.Vs, sb, u);
         su3_mult<true>(u, h, w, MU == 3 && g.antiperiodic && c == 0);
+        if (MU == 3 && g.split_t && c == 0) zero6(w);  // the neighbour lives on the previous sub-lattice
         accumulate<MU, -SF>(acc, w);
     }
 }
@@ -240,16 +247,17 @@ __device__ __forceinline__ void accumulate_scaled(C<float> (&acc)[12], const C<f
 }
 
 // one FP16 hop: neighbour spinor at index sn, link at index sl of gdir (its adjoint for
-// ADJ), projector sign S, boundary sign flip
+// ADJ), projector sign S, boundary sign flip; the links' site stride is Vl (0: Vs, the
+// spinor's, except for spinors staged in shared memory)
 template <int RECON, bool ADJ, int MU, int S, bool NC>
 __device__ __forceinline__ void hop_f16(const void *in, int Vs, int sn, const char *gdir, int sl, bool flip,
-                                        C<float> (&acc)[12]) {
+                                        C<float> (&acc)[12], int Vl = 0) {
     h2 p[12], h[6], hn[6], u[9];
     const float scale = load_raw_h2<NC>(in, Vs, sn, p);
     project_h2<MU, S>(p, h);
 #pragma unroll
     for (int k = 0; k < 6; ++k) hn[k] = h[k] ^ (ADJ ? 0x00008000u : 0x80000000u);
-    load_link_h2<RECON>(gdir, Vs, sl, u);
+    load_link_h2<RECON>(gdir, Vl ? Vl : Vs, sl, u);
     C<float> w[6];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
@@ -456,7 +464,8 @@ __device__ __forceinline__ void su3_mult1(const C<R> (&u)[9], const C<R> (&h)[3]
 
 template <int P, int RECON, bool DAG, int LO, bool NC, class R>
 __device__ __forceinline__ void half_pair(int mu, const void *in, int Vs, int nf, const char *gf, int kf, bool flip_f,
-                                          int nb, const char *gb, int kb, bool flip_b, int hh, C<R> (&acc)[9]) {
+                                          int nb, const char *gb, int kb, bool flip_b, int hh, C<R> (&acc)[9],
+                                          bool zero_f = false, bool zero_b = false) {
     constexpr int SF = DAG ? +1 : -1;
     const bool IM = mu == 0 || mu == 2;
     const bool neg = mu == 1 ? hh == 0 : mu == 2 ? hh != 0 : false;
@@ -470,6 +479,7 @@ __device__ __forceinline__ void half_pair(int mu, const void *in, int Vs, int nf
         for (int c = 0; c < 3; ++c) {
             const C<R> fd = times_f(pd[c], IM, neg);
             h[c] = cxsign(SF > 0 ? cadd(ph[c], fd) : csub(ph[c], fd), flip_f);
+            if (zero_f) h[c] = C<R>{R(0), R(0)};
         }
         LinkIO<P, RECON>::load(gf, Vs, kf, u);
         su3_mult1<false>(u, h, wf);
@@ -482,6 +492,7 @@ __device__ __forceinline__ void half_pair(int mu, const void *in, int Vs, int nf
         for (int c = 0; c < 3; ++c) {
             const C<R> fd = times_f(pd[c], IM, neg);
             h[c] = cxsign(SF > 0 ? csub(ph[c], fd) : cadd(ph[c], fd), flip_b);
+            if (zero_b) h[c] = C<R>{R(0), R(0)};
         }
         LinkIO<P, RECON>::load(gb, Vs, kb, u);
         // sum = w_f + U^dag h
@@ -508,7 +519,8 @@ __device__ __forceinline__ void half_dir(const Geom &g, const void *in, const ch
     const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
     const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
     half_pair<P, RECON, DAG, MU < 2 ? 3 : 6, NC>(MU, in, g.Vs, sf, gdir, s, MU == 3 && g.antiperiodic && c == L - 1,
-                                                sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc);
+                                                sb, gdir, sb, MU == 3 && g.antiperiodic && c == 0, hh, acc,
+                                                MU == 3 && g.split_t && c == L - 1, MU == 3 && g.split_t && c == 0);
 }
 
 template <int P, int RECON, bool DAG, int MU, bool NC, class R>
@@ -787,7 +799,19 @@ __device__ __forceinline__ void store_part(const Pt &pt, void *base, int Vs, int
 // registers); FP64 and DF32 are arithmetic-bound and keep the compiler's choice.
 template <int P> constexpr int dslash_min_blocks() { return (P == F32 || P == F16) ? 3 : 0; }
 
-// Generic Dslash kernel.  Block (bx, by) of (site_tile x rhs_tile) threads walks
+// Site tile (tile_x, in [0, gridDim.x)) and right-hand-side group (tile_y, in
+// [0, gridDim.y)) of this block.  Blocks start in linear order (x fastest); numbering
+// them with the RHS group fastest makes the blocks that share a site tile, and so its
+// links, start together: a link then comes from DRAM once and the other RHS groups find
+// it in L2, also when the gauge field is larger than L2.
+__device__ __forceinline__ int tile_x() {
+    return gridDim.y == 1 ? (int)blockIdx.x : (int)((blockIdx.y * gridDim.x + blockIdx.x) / gridDim.y);
+}
+__device__ __forceinline__ int tile_y() {
+    return gridDim.y == 1 ? (int)blockIdx.y : (int)((blockIdx.y * gridDim.x + blockIdx.x) % gridDim.y);
+}
+
+// Generic Dslash kernel.  Block (bx, by) = (tile_x, tile_y) of (site_tile x rhs_tile) threads walks
 // the site tiles bx, bx + gridDim.x, ... (grid-stride, so a grid smaller than the
 // lattice bounds the number of reduction partials); thread (x, y) handles right-hand
 // side by * rhs_tile + y, and one site (FP32, FP16) or half a site (FP64, DF32: tiles
@@ -798,7 +822,7 @@ template <int P, int RECON, bool DAG, class Ep, bool EO = false>
 __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(DslashArgs a) {
     using R = typename Real<P>::T;
     if (a.run_flag && *a.run_flag == 0) return;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int r = tile_y() * blockDim.y + threadIdx.y;
     const bool row = r < a.nrhs && row_on(a.sc, a.mask, r);
     const int rr = r < a.nrhs ? r : 0;
     const void *in = rhs_ptr<R>(a.in, a.in_stride, rr);
@@ -813,7 +837,7 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
         const int sl = ((threadIdx.x >> 5) << 4) | (threadIdx.x & 15);
         const int spb = blockDim.x >> 1;
         const SiteHalf pt{hh};
-        for (int s0 = blockIdx.x * spb; s0 < a.g.V; s0 += gridDim.x * spb) {
+        for (int s0 = tile_x() * spb; s0 < a.g.V; s0 += gridDim.x * spb) {
             const int s = s0 + sl;
             const bool on = row && s < a.g.V;
             C<R> acc[9];
@@ -831,7 +855,7 @@ __global__ void __launch_bounds__(256, dslash_min_blocks<P>()) dslash_kernel(Dsl
         }
     } else {
         const SiteAll pt{};
-        for (int s0 = blockIdx.x * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
+        for (int s0 = tile_x() * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
             const int s = s0 + threadIdx.x;
             if (row && s < a.g.V) {
                 C<R> acc[12];

@@ -23,6 +23,7 @@ extern "C" wd_status wd_apply_schur(wd_ctx *c, double kappa, const void *in, voi
     if (!c) return WD_ERR_ARG;
     c->launches = 0;
     if (!in || !out || in == out) return fail(c, WD_ERR_ARG, "wd_apply_schur: bad field pointers");
+    if (c->split) return fail(c, WD_ERR_STATE, "wd_apply_schur: not on a split sub-lattice");
     for (int mu = 0; mu < 4; ++mu)
         if (c->g.L[mu] % 2) return fail(c, WD_ERR_ARG, "wd_apply_schur: needs even extents");
     const void *gauge;

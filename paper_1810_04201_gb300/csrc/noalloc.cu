@@ -45,6 +45,7 @@ extern "C" wd_status wd_normal_apply_noalloc(wd_ctx *c, double kappa, const void
         return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: bad argument");
     if (in == out) return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: in and out must be distinct");
     if (!std::isfinite(kappa)) return fail(c, WD_ERR_ARG, "wd_normal_apply_noalloc: kappa not finite");
+    if (c->split) return fail(c, WD_ERR_STATE, "wd_normal_apply_noalloc: not on a split sub-lattice");
     const size_t need = spinor_bytes((Prec)prec, c->g.Vs) * (size_t)nrhs;
     if (need > WD_NOALLOC_SCRATCH_BYTES) {
         char msg[200];

@@ -79,10 +79,28 @@ wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes);
 Geom eo_geom(const wd_ctx *c, int parity);
 
 DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs);
+// launch shape of the solvers' fused Dslash kernels: wd_autotune_cg's choice, else tiles_for
+DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs);
+// frees a workspace buffer (no-op when absent)
+void ws_release(wd_ctx *c, const std::string &name);
+
+// The context's cache of executable CUDA graphs (solver plans keyed by their signature:
+// precision, tiles, kappa, ...).  It holds at most kMaxGraphs; graph_put evicts the least
+// recently used one (a graph still executing is freed by CUDA when it completes), so a
+// caller that scans kappa or many masses does not grow it without bound.
+constexpr size_t kMaxGraphs = 16;
+void *graph_get(wd_ctx *c, const std::string &key);  // nullptr when absent; marks it used
+void graph_put(wd_ctx *c, const std::string &key, void *exec, const std::vector<long long> &info);
+void graph_clear(wd_ctx *c);
 
 // Launchers of the plain operators (xpay epilogue): out = in - kappa * hop
 // (dagger = 0: D, dagger = 1: D^dag).  Used by wd_apply and the autotuner.
 cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, DslashTiles t, cudaStream_t st);
+// The same operator with the neighbour spinors staged through shared memory (FP32, FP16;
+// tiles of `rows` x-rows, `stages` tiles in flight per block); err: set to 1 when a wait runs out.
+cudaError_t launch_apply_staged(const DslashArgs &a, Prec p, int recon, bool dagger, int rows, int stages,
+                                unsigned *err, cudaStream_t st);
+bool staged_ok(Prec p, const Geom &g, int rows, int stages);
 
 // Kernel-node description for graph building and direct launches.
 struct KernelCall {

@@ -78,6 +78,8 @@ struct Geom {
     int antiperiodic;
     int eo_parity;   // -1: full lattice; 0 / 1: checkerboard fields, output on this parity
     unsigned *dbg;   // debug builds: the context's word for the first out-of-range index
+    int split_t;     // 1: one sub-lattice of a lattice split along t; the t hops that leave it
+                     // (from the first slice backward, from the last slice forward) are omitted
 };
 
 // Index checks of debug builds (compiled with -DWD_DEBUG, in place of a memory checker):
@@ -547,8 +549,18 @@ struct wd_ctx {
     std::map<std::string, size_t> ws_size;
     std::map<std::string, void *> graphs;              // cached cudaGraphExec_t per solver signature
     std::map<std::string, std::vector<long long>> graph_info;
+    std::map<std::string, unsigned long long> graph_used;  // last use of each graph (graph_get / graph_put)
+    unsigned long long graph_tick = 0;
     std::map<int, wd::DslashTiles> tiles;              // key: prec*64 + nrhs
+    std::map<int, wd::DslashTiles> cg_tiles;           // the solvers' fused kernels (wd_autotune_cg); same key
+    int staged_rows[wd::kNumPrec] = {};                // plain operators through the staged kernel (0: off)
+    int staged_stages[wd::kNumPrec] = {};
     void *noalloc_scratch = nullptr;                   // device address of the allocation-free scratch array
+    // one sub-lattice of a lattice split along t (wd_create_split): ranks own consecutive
+    // blocks of global t-slices; g.split_t is set and g.antiperiodic is 0 (the global
+    // boundary sign is applied to the faces received across it)
+    bool split = false;
+    int split_rank = 0, split_nranks = 1, split_antiperiodic = 0, split_t0 = 0;
     ~wd_ctx();
 };
 

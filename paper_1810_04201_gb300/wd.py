@@ -40,6 +40,16 @@ class CGResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class Comm(ctypes.Structure):
+    """wd_comm: the callbacks through which a split solve reaches other processes."""
+    _fields_ = [("user", ctypes.c_void_p), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN)]
+
+
 class WDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -80,8 +90,18 @@ def load_library(path: str = LIB_PATH):
                                  ctypes.POINTER(CGResult)], I),
         "wd_autotune": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "wd_set_tiles": ([P, I, I, I, I], I),
+        "wd_autotune_cg": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "wd_set_staging": ([P, I, I, I], I),
+        "wd_staging_error": ([P, ctypes.POINTER(ctypes.c_uint)], I),
         "wd_kernel_launches": ([P], ctypes.c_longlong),
         "wd_measure_fp64_rate": ([ctypes.POINTER(D)], I),
+        "wd_create_split": ([ctypes.POINTER(P), ctypes.POINTER(I), I, I, I, P], I),
+        "wd_face_bytes": ([P, I, I], S),
+        "wd_face_pack": ([P, P, P, P, I, I, I], I),
+        "wd_apply_interior": ([P, D, P, P, I, I, I], I),
+        "wd_apply_faces": ([P, D, P, P, P, I, I, I], I),
+        "wd_cg_solve_split": ([PP, I, D, PP, PP, ctypes.POINTER(CGParams), ctypes.POINTER(CGResult),
+                               ctypes.POINTER(Comm)], I),
         "wd_status_string": ([I], ctypes.c_char_p),
         "wd_last_error": ([P], ctypes.c_char_p),
     }
@@ -278,8 +298,196 @@ class Lattice:
             TileCache(path).put(key, (st_.value, rt.value))
         return st_.value, rt.value
 
+    def autotune_cg(self, prec=WD_F64, nrhs=1):
+        """Tune the launch shape of the solver's fused kernels for inner precision prec
+        (wd_autotune_cg); returns (site_tile, rhs_tile)."""
+        st_, rt = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wd_autotune_cg(self.ctx, prec, nrhs, ctypes.byref(st_), ctypes.byref(rt)),
+                    "wd_autotune_cg")
+        return st_.value, rt.value
+
+    def set_staging(self, prec, rows, stages=2):
+        """Plain operators of precision prec through the staged kernel (rows > 0) or the
+        direct-load one (rows = 0)."""
+        self._check(self.lib.wd_set_staging(self.ctx, prec, int(rows), int(stages)), "wd_set_staging")
+
+    def staging_error(self) -> int:
+        w = ctypes.c_uint()
+        self._check(self.lib.wd_staging_error(self.ctx, ctypes.byref(w)), "wd_staging_error")
+        return int(w.value)
+
     def set_tiles(self, prec, nrhs, site_tile, rhs_tile):
         self._check(self.lib.wd_set_tiles(self.ctx, prec, nrhs, site_tile, rhs_tile), "wd_set_tiles")
+
+
+class TSplit:
+    """A lattice split along t into nranks sub-lattices (section 2.3): which global t-slices
+    each rank owns, its neighbours, the sign of the global antiperiodic boundary on what it
+    receives, and the face exchange and global sums over torch.distributed.  Host logic
+    only: the faces themselves are packed and applied by the library's kernels."""
+
+    def __init__(self, dims, nranks):
+        self.dims = tuple(int(d) for d in dims)
+        self.nranks = int(nranks)
+        if self.nranks < 2 or self.dims[3] % self.nranks:
+            raise ValueError("the t extent must split into nranks >= 2 equal blocks")
+        self.lt = self.dims[3] // self.nranks
+        self.vf = self.dims[0] * self.dims[1] * self.dims[2]  # sites of one t-slice (a face)
+
+    def t_range(self, rank):
+        """Global t-slices [t0, t1) of rank."""
+        return rank * self.lt, (rank + 1) * self.lt
+
+    def neighbours(self, rank):
+        """(previous, next) rank along t, periodic."""
+        return (rank - 1) % self.nranks, (rank + 1) % self.nranks
+
+    def receive_signs(self, rank, antiperiodic=True):
+        """Signs on what rank receives from (previous, next): -1 across the global boundary
+        t = T-1 <-> 0 of an antiperiodic lattice."""
+        s = -1.0 if antiperiodic else 1.0
+        return (s if rank == 0 else 1.0), (s if rank == self.nranks - 1 else 1.0)
+
+    def local_sites(self, rank):
+        """Global site indices of rank's sub-lattice, in its local order (x fastest, t slowest)."""
+        t0, t1 = self.t_range(rank)
+        return np.arange(t0 * self.vf, t1 * self.vf)
+
+    def local_field(self, psi, rank):
+        """Rank's part of a canonical global field (..., V, 4, 3)."""
+        t0, t1 = self.t_range(rank)
+        return np.ascontiguousarray(psi[..., t0 * self.vf:t1 * self.vf, :, :])
+
+    def local_links(self, U, rank):
+        """Rank's links U_mu(n) for its own sites n, (4, V_local, 3, 3)."""
+        t0, t1 = self.t_range(rank)
+        return np.ascontiguousarray(U[:, t0 * self.vf:t1 * self.vf])
+
+    @staticmethod
+    def exchange(dist, rank, prev, nxt, send_prev, recv_prev, send_next, recv_next, group=None):
+        """Faces between neighbouring processes, in two shifts so that every message pairs
+        with its receive even when prev == next (two processes): first each process sends
+        send_next forward and receives recv_prev from behind, then send_prev backward and
+        recv_next from ahead.  Tensors (CPU for gloo, CUDA for NCCL)."""
+        if prev == rank and nxt == rank:
+            recv_prev.copy_(send_next)
+            recv_next.copy_(send_prev)
+            return
+        for snd, dst, rcv, src in ((send_next, nxt, recv_prev, prev), (send_prev, prev, recv_next, nxt)):
+            if dist.get_backend(group) == "nccl":
+                ops = [dist.P2POp(dist.isend, snd, dst, group), dist.P2POp(dist.irecv, rcv, src, group)]
+                for w in dist.batch_isend_irecv(ops):
+                    w.wait()
+            else:
+                ws = [dist.isend(snd, dst, group=group), dist.irecv(rcv, src, group=group)]
+                for w in ws:
+                    w.wait()
+
+    @staticmethod
+    def allreduce_sum(dist, t, group=None):
+        """In-place sum of a tensor over all processes."""
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t
+
+
+class SplitLattice(Lattice):
+    """The sub-lattice of one rank of a lattice split along t (wd_create_split)."""
+
+    def __init__(self, dims, nranks, rank, antiperiodic_t=True, stream=None):
+        self.lib = load_library()
+        self.split = TSplit(dims, nranks)
+        self.rank = int(rank)
+        self.dims = self.split.dims[:3] + (self.split.lt,)
+        self.global_dims = self.split.dims
+        self.V = int(np.prod(self.dims))
+        self.ctx = ctypes.c_void_p()
+        self.recon = 18
+        self.recon_p = {}
+        d = (ctypes.c_int * 4)(*self.global_dims)
+        st = self.lib.wd_create_split(ctypes.byref(self.ctx), d, int(nranks), int(rank), int(bool(antiperiodic_t)),
+                                      _stream_ptr(stream))
+        if st != 0:
+            raise WDError(st, "wd_create_split failed")
+
+    def face_bytes(self, prec=WD_F64, nrhs=1) -> int:
+        return int(self.lib.wd_face_bytes(self.ctx, prec, nrhs))
+
+    def new_face(self, prec=WD_F64, nrhs=1):
+        return torch.zeros(self.face_bytes(prec, nrhs), dtype=torch.uint8, device="cuda")
+
+    def face_pack(self, src, to_prev, to_next, prec=WD_F64, nrhs=1, dagger=False):
+        self._check(self.lib.wd_face_pack(self.ctx, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(to_prev.data_ptr()),
+                                          ctypes.c_void_p(to_next.data_ptr()), prec, nrhs, int(bool(dagger))),
+                    "wd_face_pack")
+
+    def apply_interior(self, kappa, src, dst, prec=WD_F64, nrhs=1, dagger=False):
+        self._check(self.lib.wd_apply_interior(self.ctx, float(kappa), ctypes.c_void_p(src.data_ptr()),
+                                               ctypes.c_void_p(dst.data_ptr()), prec, nrhs, int(bool(dagger))),
+                    "wd_apply_interior")
+        return dst
+
+    def apply_faces(self, kappa, from_prev, from_next, dst, prec=WD_F64, nrhs=1, dagger=False):
+        self._check(self.lib.wd_apply_faces(self.ctx, float(kappa), ctypes.c_void_p(from_prev.data_ptr()),
+                                            ctypes.c_void_p(from_next.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                            prec, nrhs, int(bool(dagger))), "wd_apply_faces")
+        return dst
+
+
+def _cuda_bytes(ptr, n):
+    """A torch uint8 CUDA tensor over n bytes of device memory at ptr (no copy)."""
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (int(n),), "typestr": "|u1", "data": (int(ptr), False), "version": 3}
+    return torch.as_tensor(_Arr(), device="cuda")
+
+
+class DistComm:
+    """wd_comm over torch.distributed for split solves spread over processes (one
+    sub-lattice block per process): faces through TSplit.exchange, sums through all_reduce.
+    Keeps its ctypes callbacks alive while it exists."""
+
+    def __init__(self, dist, split: TSplit, first_rank, last_rank, proc_of_rank, group=None):
+        self.dist, self.split, self.group = dist, split, group
+        me = dist.get_rank(group)
+        self.me = me
+        self.prev = proc_of_rank(split.neighbours(first_rank)[0])
+        self.next = proc_of_rank(split.neighbours(last_rank)[1])
+
+        def exchange(user, send_prev, recv_prev, send_next, recv_next, nbytes, stream):
+            try:
+                t = [_cuda_bytes(p, nbytes) for p in (send_prev, recv_prev, send_next, recv_next)]
+                TSplit.exchange(self.dist, self.me, self.prev, self.next, t[0], t[1], t[2], t[3], self.group)
+                return 0
+            except Exception:  # a failed exchange is reported through the status, never raised through C
+                return 1
+
+        def allreduce(user, vals, n):
+            try:
+                dev = "cuda" if self.dist.get_backend(self.group) == "nccl" else "cpu"
+                t = torch.tensor([vals[i] for i in range(n)], dtype=torch.float64, device=dev)
+                TSplit.allreduce_sum(self.dist, t, self.group)
+                for i, v in enumerate(t.cpu().tolist()):
+                    vals[i] = v
+                return 0
+            except Exception:
+                return 1
+
+        self._cb = (EXCHANGE_FN(exchange), ALLREDUCE_FN(allreduce))
+        self.struct = Comm(None, self._cb[0], self._cb[1])
+
+
+def cg_split(lattices, kappa, bs, xs, tol=1e-10, max_iter=10000, comm=None):
+    """CGNR on a lattice split along t (wd_cg_solve_split): lattices are this process's
+    SplitLattice blocks (consecutive ranks); comm a DistComm when other processes hold the rest."""
+    lib = load_library()
+    n = len(lattices)
+    ctxs = (ctypes.c_void_p * n)(*[L.ctx.value for L in lattices])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    p = CGParams(tol, max_iter, WD_F64, 0.0, 1, 0, 0, 0, 0, 0)
+    res = CGResult()
+    st = lib.wd_cg_solve_split(ctxs, n, float(kappa), bp, xp, ctypes.byref(p), ctypes.byref(res),
+                               ctypes.byref(comm.struct) if comm is not None else None)
+    return res.as_dict(), st
 
 
 def measure_fp64_rate() -> float:

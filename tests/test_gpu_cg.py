@@ -527,3 +527,44 @@ def test_stop_rule_arguments(wd):
     r2, _ = lat.cg(0.12, b, fx2, normal_eq=1, stop_rule=1)
     assert r1[0]["iters"] == r2[0]["iters"]
     assert np.array_equal(lat.unpack(fx1), lat.unpack(fx2))
+
+
+def test_kappa_scan_keeps_graph_cache_bounded(wd):
+    """kappa is part of a solver graph's signature: a scan over 20 values (more than the 16
+    graphs a context keeps) evicts the least recently used graphs and every solve still
+    gives the oracle's solution, also a kappa whose graph was evicted and is rebuilt."""
+    dims = (4, 4, 4, 4)
+    U = gen.haar_links(dims, seed=81)
+    b = gen.gaussian_source(dims, seed=82)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb = lat.pack(b)
+    kappas = [0.10 + 0.00125 * i for i in range(20)] + [0.10]
+    for k in kappas:
+        fx = lat.new_field()
+        res, st = lat.cg(k, fb, fx, tol=1e-10)
+        assert st == 0 and res[0]["true_rel_resid"] <= 1e-10
+        x_ref, _ = ref_solution(U, b, k, dims)
+        assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9, k
+
+
+@pytest.mark.parametrize("inner,nrhs", [(0, 1), (1, 1), (1, 3)])
+def test_autotune_cg_keeps_solutions(wd, inner, nrhs):
+    """The solver autotuner picks a valid launch shape for the fused CG kernels; solves with
+    it give the oracle's solutions, and the plain operator's shape is left as it was."""
+    dims, kappa = (8, 8, 4, 8), 0.12
+    U = gen.haar_links(dims, seed=83)
+    B = gen.gaussian_source(dims, seed=84, nrhs=nrhs)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    plain = lat.autotune(inner, nrhs)
+    st_, rt = lat.autotune_cg(inner, nrhs)
+    assert st_ in (16, 32, 64, 128, 256) and 1 <= rt <= nrhs and (st_ * rt) % 32 == 0 and st_ * rt <= 256
+    assert plain[0] in (16, 32, 64, 128, 256)
+    fx = lat.new_field(nrhs=nrhs)
+    res, st = lat.cg(kappa, lat.pack(B if nrhs > 1 else B[0]), fx, tol=1e-10, inner=inner, nrhs=nrhs)
+    assert st == 0
+    X = lat.unpack(fx, nrhs=nrhs, squeeze=False)
+    for j in range(nrhs):
+        x_ref, _ = ref_solution(U, B[j], kappa, dims)
+        assert oracle.rel_err(X[j], x_ref) < 1e-9
