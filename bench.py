@@ -364,8 +364,11 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="with --dslash-only: autotune the launch shape first")
-    ap.add_argument("--staged", default=None, metavar="ROWS[,STAGES]",
-                    help="with --dslash-only: the kernel with neighbour spinors staged through shared memory")
+    ap.add_argument("--staged", default=None, metavar="R,S[;R,S...]",
+                    help="with --dslash-only: time the kernel with neighbour spinors staged through shared memory, "
+                         "R rows per tile and S stages, for each listed pair (0: the direct-load kernel)")
+    ap.add_argument("--block", action="store_true",
+                    help="with --compare on c1-c3: also block CG on 12 Gaussian sources against 12 sequential solves")
     ap.add_argument("--compare", action="store_true",
                     help="c3: FP64 vs FP32 vs FP16-storage solves; c4: 12 sequential FP64 solves vs multi-RHS "
                          "and block CG; c5: batched persistent solve vs one-at-a-time FP64 solves")
@@ -788,6 +791,8 @@ def compare(args):
                 continue
             line["compare"][name]["rel_diff_vs_f64_solution"] = rel_diff(sols[name], sols["f64"])
             line["compare"][name]["speedup_vs_f64"] = round(line["compare"]["f64"]["ms"] / line["compare"][name]["ms"], 3)
+        if args.block:
+            line["compare"]["block_cg_12_sources"] = block_vs_sequential(wd, torch, lat, w, reps)
         line["note"] = ("gflops counts 1320 flop/site per full-lattice operator application; an even-odd "
                         "iteration applies the Schur operator twice, counted as 2 * 1320 * V / 2 * 2 flop")
     else:  # c4: 12 point sources
@@ -828,8 +833,42 @@ def compare(args):
     print(json.dumps(line))
 
 
+def block_vs_sequential(wd, torch, lat, w, reps):
+    """Block CG (one Krylov space for 12 Gaussian sources, FP64) against 12 sequential FP64
+    solves on the same lattice, each to a true normal residual of 1e-10."""
+    from paper_1810_04201_gb300 import gen
+    B = np.stack([gen.gaussian_source(w["dims"], w["seed"] + 100 + k) for k in range(12)])
+    fb = lat.pack(B)
+    fbs = [lat.pack(B[k]) for k in range(12)]
+    fys = [lat.new_field() for _ in range(12)]
+
+    def seq():
+        out = []
+        for k in range(12):
+            fys[k].zero_()
+            out.append(lat.cg(w["kappa"], fbs[k], fys[k], tol=1e-10)[0][0])
+        return out
+
+    ms_seq, res_seq = _timed_solves(torch, seq, reps)
+    fx = lat.new_field(nrhs=12)
+
+    def blk():
+        fx.zero_()
+        return lat.cg(w["kappa"], fb, fx, tol=1e-10, nrhs=12, block=1, raise_on_fail=False)
+
+    ms_blk, (res_blk, st) = _timed_solves(torch, blk, reps)
+    X = lat.unpack(fx, nrhs=12, squeeze=False)
+    return {"sequential_f64_ms": round(ms_seq, 3), "sequential_iters_max": max(r["iters"] for r in res_seq),
+            "block_cg_f64_ms": round(ms_blk, 3), "block_iters": max(r["iters"] for r in res_blk), "status": st,
+            "block_max_true_rel_resid": max(r["true_rel_resid"] for r in res_blk),
+            "speedup_block_vs_sequential": round(ms_seq / ms_blk, 3),
+            "max_rel_diff_vs_sequential": max(rel_diff(X[k], lat.unpack(fys[k])) for k in range(12))}
+
+
 def dslash_only(args):
-    """W warm-up and K timed launches of one Dslash (D, xpay) on a Haar lattice."""
+    """W warm-up and K timed launches of one Dslash (D, xpay) on a Haar lattice; with
+    --staged "R,S;R,S;..." each listed configuration of the staged kernel (R rows per tile,
+    S stages; "0" the direct-load kernel) is timed in turn, one JSON line each."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -839,35 +878,36 @@ def dslash_only(args):
     lat.set_gauge(gen.haar_links(dims, 3), recon=args.recon)
     b = gen.gaussian_source(dims, 4, nrhs=args.nrhs)
     pid = PREC_ID[args.prec]
-    tiles = lat.autotune(pid, args.nrhs) if args.autotune else None
-    if args.staged:
-        parts = [int(v) for v in args.staged.split(",")]
-        lat.set_staging(pid, parts[0], parts[1] if len(parts) > 1 else 2)
-        tiles = {"staged_rows": parts[0], "stages": parts[1] if len(parts) > 1 else 2}
+    tuned = lat.autotune(pid, args.nrhs) if args.autotune else None
     fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
     fo = lat.new_field(pid, args.nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        lat.apply(0.12, fi, fo, pid, args.nrhs)
-    ts = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lat.apply(0.12, fi, fo, pid, args.nrhs)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ms = statistics.mean(ts)
-    if args.staged and lat.staging_error():
-        raise RuntimeError("a wait of the staged kernel ran out")
-    V = lat.V
-    nb = V * (args.nrhs * 2 * SPINOR_BYTES[args.prec] + LINK_BYTES[(args.prec, args.recon)])
-    print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs, "tiles": tiles,
-                      "ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V * args.nrhs / ms / 1e6, 1),
-                      "algorithmic_gbs": round(nb / ms / 1e6, 1), "bytes_per_launch": nb}))
+    configs = [[int(v) for v in c.split(",")] for c in args.staged.split(";")] if args.staged else [[0]]
+    for cfg in configs:
+        rows, stages = cfg[0], (cfg[1] if len(cfg) > 1 else 2)
+        lat.set_staging(pid, rows, stages) if rows else lat.set_staging(pid, 0)
+        tiles = {"staged_rows": rows, "stages": stages} if rows else tuned
+        for _ in range(args.warmup):
+            lat.apply(0.12, fi, fo, pid, args.nrhs)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.apply(0.12, fi, fo, pid, args.nrhs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.mean(ts)
+        if rows and lat.staging_error():
+            raise RuntimeError("a wait of the staged kernel ran out")
+        V = lat.V
+        nb = V * (args.nrhs * 2 * SPINOR_BYTES[args.prec] + LINK_BYTES[(args.prec, args.recon)])
+        print(json.dumps({"dslash": list(dims), "prec": args.prec, "recon": args.recon, "nrhs": args.nrhs,
+                          "tiles": tiles, "ms": round(ms, 5), "gflops": round(FLOP_PER_SITE * V * args.nrhs / ms / 1e6, 1),
+                          "algorithmic_gbs": round(nb / ms / 1e6, 1), "bytes_per_launch": nb}), flush=True)
 
 
 def sweep(wd, torch, flush, stream, recon):

@@ -389,6 +389,16 @@ wd_status wd_cg_solve_split(wd_ctx *const *ctxs, int n, double kappa, const void
  * changes no device setting.  Errors: WD_ERR_ARG (null), WD_ERR_CUDA. */
 wd_status wd_measure_fp64_rate(double *gflops);
 
+/* The launch shape the plain operators of (prec, nrhs) use now: site_tile, rhs_tile and
+ * rhs_per_thread (any pointer may be NULL). */
+wd_status wd_get_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile, int *rhs_per_thread);
+/* Plain FP32 operators: each thread applies its site's links to k (1 to 4) of its block's
+ * right-hand sides, loading each link once for all k (k dividing rhs_tile, and
+ * site_tile * rhs_tile / k threads a multiple of 32); wd_autotune considers k = 2, 3, 4
+ * beside 1.  Other precisions and the solvers' fused kernels: k = 1 only.  No counterpart in
+ * the paper, which has one right-hand side. */
+wd_status wd_set_rhs_per_thread(wd_ctx *ctx, wd_prec prec, int nrhs, int k);
+
 /* Launch-configuration query: number of kernel launches the last wd_* call queued
  * (graph kernel nodes count once per execution). */
 long long wd_kernel_launches(const wd_ctx *ctx);

@@ -283,4 +283,16 @@ template <int DUMMY = 0> __global__ void k_join_eo(EoVecArgs e) {
     SpinorIO<F64>::store(rp(v.b, v.b_stride, r), v.Vs, n, x);
 }
 
+// A deterministic non-zero buffer (values in [-1, 1) from a hash of the index): the input of
+// the autotuners, so that no candidate is timed on zeros.  For FP16 fields of reals it
+// fills every 32-bit word with a float in [-1, 1), scales included.
+template <class T> __global__ void k_fill_hash(T *p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 31)) * 0xD6E8FEB86659FD93ull;
+        z ^= z >> 32;
+        p[i] = (T)((double)(z >> 11) * 0x1.0p-52 - 1.0);
+    }
+}
+
 }  // namespace wd

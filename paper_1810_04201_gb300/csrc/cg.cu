@@ -58,17 +58,6 @@ static cudaError_t run_host_loop(wd_ctx *c, const Plan &plan, const Fields &f, i
 wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_cg_params *prm,
                          wd_cg_result *res);
 
-// A deterministic non-zero FP64 field (values in [-1, 1) from a hash of the index), the
-// right-hand side of the solver autotuner.
-__global__ void k_fill_hash(double *p, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 31)) * 0xD6E8FEB86659FD93ull;
-        z ^= z >> 32;
-        p[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
-    }
-}
-
 }  // namespace wd
 
 extern "C" {
@@ -313,7 +302,7 @@ wd_status wd_autotune_cg(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int 
     if ((s = ws_get(c, "tunecg_b", fb, &b)) != WD_OK) return s;
     if ((s = ws_get(c, "tunecg_x", fb, &x)) != WD_OK) return s;
     if ((s = ws_get(c, "tunecg_flush", flush_bytes, &flush)) != WD_OK) return s;
-    k_fill_hash<<<1024, 256, 0, c->stream>>>(static_cast<double *>(b), fb / sizeof(double));
+    k_fill_hash<double><<<1024, 256, 0, c->stream>>>(static_cast<double *>(b), fb / sizeof(double));
     WD_CUDA(c, cudaGetLastError());
     wd_cg_params prm{};
     prm.tol = 1e-20;  // never met: every candidate runs max_iter iterations

@@ -911,4 +911,84 @@ template <class R, int N> __device__ __forceinline__ double norm2_of(const C<R> 
     return n;
 }
 
+// ---------------------------------------------------------------- K right-hand sides per thread
+// The plain FP32 operator with each thread applying its site's links to K right-hand sides:
+// a link is loaded once and multiplies K projected half spinors, so per site and right-hand
+// side the loads of links (288 bytes, 40 instructions) fall K-fold; the spinor loads are the
+// same.  Rows past nrhs (a partial last group) read a valid row and store nothing.
+template <int RECON, bool DAG, int MU, int K>
+__device__ __forceinline__ void hop_dir_k(const DslashArgs &a, const char *gdir, const int (&row)[K], int s, int c,
+                                          C<float> (&acc)[K][12]) {
+    constexpr int SF = DAG ? +1 : -1;
+    const Geom &g = a.g;
+    const int L = g.L[MU], st = g.stride[MU];
+    {
+        const int sf = WD_IDX(g, (c == L - 1) ? s - (L - 1) * st : s + st, g.V, 1);
+        C<float> u[9];
+        LinkIO<F32, RECON>::load(gdir, g.Vs, s, u);
+        const bool flip = MU == 3 && g.antiperiodic && c == L - 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            C<float> p[12], h[6], w[6];
+            SpinorIO<F32>::load(rhs_ptr<float>(a.in, a.in_stride, row[k]), g.Vs, sf, p);
+            project<MU, SF>(p, h);
+            su3_mult<false>(u, h, w, flip);
+            accumulate<MU, SF>(acc[k], w);
+        }
+    }
+    {
+        const int sb = WD_IDX(g, (c == 0) ? s + (L - 1) * st : s - st, g.V, 2);
+        C<float> u[9];
+        LinkIO<F32, RECON>::load(gdir, g.Vs, sb, u);
+        const bool flip = MU == 3 && g.antiperiodic && c == 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            C<float> p[12], h[6], w[6];
+            SpinorIO<F32>::load(rhs_ptr<float>(a.in, a.in_stride, row[k]), g.Vs, sb, p);
+            project<MU, -SF>(p, h);
+            su3_mult<true>(u, h, w, flip);
+            accumulate<MU, -SF>(acc[k], w);
+        }
+    }
+}
+
+template <int RECON, bool DAG, int K>
+__global__ void __launch_bounds__(256) dslash_multi_kernel(DslashArgs a) {
+    const int r0 = (tile_y() * blockDim.y + threadIdx.y) * K;
+    if (r0 >= a.nrhs) return;  // no block-wide step follows
+    int row[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) row[k] = r0 + k < a.nrhs ? r0 + k : a.nrhs - 1;
+    const char *gb = reinterpret_cast<const char *>(a.gauge);
+    for (int s0 = tile_x() * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        if (s >= a.g.V) continue;
+        int rem = s;
+        const int x = rem % a.g.L[0]; rem /= a.g.L[0];
+        const int y = rem % a.g.L[1]; rem /= a.g.L[1];
+        const int z = rem % a.g.L[2];
+        const int t = rem / a.g.L[2];
+        C<float> acc[K][12];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[k][c] = C<float>{0.f, 0.f};
+        hop_dir_k<RECON, DAG, 0, K>(a, gb, row, s, x, acc);
+        hop_dir_k<RECON, DAG, 1, K>(a, gb + a.gauge_dir, row, s, y, acc);
+        hop_dir_k<RECON, DAG, 2, K>(a, gb + 2 * a.gauge_dir, row, s, z, acc);
+        hop_dir_k<RECON, DAG, 3, K>(a, gb + 3 * a.gauge_dir, row, s, t, acc);
+        const float kap = (float)a.kappa;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (r0 + k >= a.nrhs) break;
+            C<float> p[12];
+            SpinorIO<F32>::load(a.xsrc ? rhs_ptr<float>(a.xsrc, a.xsrc_stride, row[k]) : rhs_ptr<float>(a.in, a.in_stride, row[k]),
+                                a.g.Vs, s, p);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) p[c] = C<float>{p[c].re - kap * acc[k][c].re, p[c].im - kap * acc[k][c].im};
+            SpinorIO<F32>::store(rhs_ptr<float>(a.out, a.out_stride, row[k]), a.g.Vs, s, p);
+        }
+    }
+}
+
 }  // namespace wd

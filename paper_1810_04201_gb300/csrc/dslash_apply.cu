@@ -7,6 +7,17 @@ namespace wd {
 
 template <int P, int RECON, bool DAG>
 static cudaError_t go(const DslashArgs &a, DslashTiles t, cudaStream_t st) {
+    if constexpr (P == F32) {
+        const int k = t.rhs_per_thread;
+        if (k > 1 && t.rhs_tile % k == 0) {
+            dim3 block(t.site_tile, t.rhs_tile / k);
+            dim3 grid(site_blocks<P>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+            if (k == 2) dslash_multi_kernel<RECON, DAG, 2><<<grid, block, 0, st>>>(a);
+            else if (k == 3) dslash_multi_kernel<RECON, DAG, 3><<<grid, block, 0, st>>>(a);
+            else dslash_multi_kernel<RECON, DAG, 4><<<grid, block, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     dim3 block(t.site_tile, t.rhs_tile);
     dim3 grid(site_blocks<P>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
     dslash_kernel<P, RECON, DAG, EpXpay><<<grid, block, 0, st>>>(a);

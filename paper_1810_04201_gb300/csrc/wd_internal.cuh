@@ -527,7 +527,10 @@ inline double default_delta(Prec p) {
     }
 }
 
-struct DslashTiles { int site_tile = 128; int rhs_tile = 1; };
+// Launch shape of a Dslash: blocks of site_tile x rhs_tile (site, right-hand side) pairs; with
+// rhs_per_thread = K > 1 (plain FP32 operator) each thread takes K of the block's right-hand
+// sides, so the block has site_tile x rhs_tile / K threads and loads each link once for K.
+struct DslashTiles { int site_tile = 128; int rhs_tile = 1; int rhs_per_thread = 1; };
 
 }  // namespace wd
 

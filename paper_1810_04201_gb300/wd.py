@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
         "wd_set_tiles": ([P, I, I, I, I], I),
         "wd_autotune_cg": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "wd_set_staging": ([P, I, I, I], I),
+        "wd_get_tiles": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "wd_set_rhs_per_thread": ([P, I, I, I], I),
         "wd_staging_error": ([P, ctypes.POINTER(ctypes.c_uint)], I),
         "wd_kernel_launches": ([P], ctypes.c_longlong),
         "wd_measure_fp64_rate": ([ctypes.POINTER(D)], I),
@@ -305,6 +307,16 @@ class Lattice:
         self._check(self.lib.wd_autotune_cg(self.ctx, prec, nrhs, ctypes.byref(st_), ctypes.byref(rt)),
                     "wd_autotune_cg")
         return st_.value, rt.value
+
+    def tiles(self, prec=WD_F64, nrhs=1):
+        """(site_tile, rhs_tile, rhs_per_thread) the plain operators of (prec, nrhs) use."""
+        a, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wd_get_tiles(self.ctx, prec, nrhs, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)),
+                    "wd_get_tiles")
+        return a.value, b.value, k.value
+
+    def set_rhs_per_thread(self, prec, nrhs, k):
+        self._check(self.lib.wd_set_rhs_per_thread(self.ctx, prec, nrhs, int(k)), "wd_set_rhs_per_thread")
 
     def set_staging(self, prec, rows, stages=2):
         """Plain operators of precision prec through the staged kernel (rows > 0) or the

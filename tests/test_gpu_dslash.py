@@ -241,7 +241,7 @@ def test_staged_dslash_matches_oracle(wd, prec, dims, rows):
             lat.set_staging(prec, staged, 3 if staged else 2)
             for dag in (False, True):
                 o = lat.new_field(prec, nrhs=2)
-                (lat.apply_dagger if dag else lat.apply)(0.12, f, o, prec, nrhs=2)
+                lat.apply(0.12, f, o, prec, nrhs=2, dagger=dag)
                 got = lat.unpack(o, prec, nrhs=2)
                 if not staged:
                     direct[dag] = got
@@ -267,3 +267,34 @@ def test_staged_dslash_rejects_unsuited_shapes(wd):
         big.set_staging(1, 8, 2)
     lat.set_staging(1, 2, 2)
     lat.set_staging(1, 0)
+
+
+@pytest.mark.parametrize("nrhs,site_tile,rhs_tile,k", [(3, 32, 3, 3), (8, 32, 8, 2), (8, 64, 4, 4), (12, 16, 8, 4),
+                                                       (12, 32, 6, 3), (5, 64, 4, 2)])
+def test_rhs_per_thread_matches_oracle(wd, nrhs, site_tile, rhs_tile, k):
+    """FP32 with k right-hand sides per thread (each link loaded once for k): D and D^dag
+    against the oracle, also with a partial last group of right-hand sides, and the same
+    result as one right-hand side per thread."""
+    dims = (6, 4, 4, 6)
+    U = gen.haar_links(dims, seed=95)
+    psi = gen.gaussian_source(dims, seed=96, nrhs=nrhs)
+    for recon in (18, 12):
+        lat = wd.Lattice(dims)
+        lat.set_gauge(U, recon=recon)
+        f = lat.pack(psi, 1)
+        lat.set_tiles(1, nrhs, site_tile, rhs_tile)
+        outs = {}
+        for kk in (1, k):
+            lat.set_rhs_per_thread(1, nrhs, kk)
+            assert lat.tiles(1, nrhs) == (site_tile, rhs_tile, kk)
+            for dag in (False, True):
+                o = lat.new_field(1, nrhs=nrhs)
+                lat.apply(0.12, f, o, 1, nrhs=nrhs, dagger=dag)
+                outs[kk, dag] = lat.unpack(o, 1, nrhs=nrhs)
+        for dag in (False, True):
+            for j in range(nrhs):
+                want = oracle.apply_D(U, psi[j], 0.12, dims, dagger=dag)
+                assert oracle.rel_err(outs[k, dag][j], want) < TOL[1], (recon, dag, j)
+            assert oracle.rel_err(outs[k, dag], outs[1, dag]) < 1e-7
+    with pytest.raises(wd.WDError):
+        lat.set_rhs_per_thread(0, nrhs, 2)  # FP64: one right-hand side per thread
