@@ -364,6 +364,8 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="with --dslash-only: autotune the launch shape first")
+    ap.add_argument("--tiles", default=None, metavar="ST,RT[,K]",
+                    help="with --dslash-only: fix the launch shape (site tile, RHS tile, RHS per thread)")
     ap.add_argument("--staged", default=None, metavar="R,S[;R,S...]",
                     help="with --dslash-only: time the kernel with neighbour spinors staged through shared memory, "
                          "R rows per tile and S stages, for each listed pair (0: the direct-load kernel)")
@@ -879,6 +881,12 @@ def dslash_only(args):
     b = gen.gaussian_source(dims, 4, nrhs=args.nrhs)
     pid = PREC_ID[args.prec]
     tuned = lat.autotune(pid, args.nrhs) if args.autotune else None
+    if args.tiles:
+        t = [int(v) for v in args.tiles.split(",")]
+        lat.set_tiles(pid, args.nrhs, t[0], t[1])
+        if len(t) > 2:
+            lat.set_rhs_per_thread(pid, args.nrhs, t[2])
+        tuned = list(lat.tiles(pid, args.nrhs))
     fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
     fo = lat.new_field(pid, args.nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
