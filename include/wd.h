@@ -289,9 +289,10 @@ wd_status wd_autotune(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *
  * Dslash with the CG epilogues and reductions) as wd_cg_solve runs them -- ten iterations
  * of the device-resident loop in inner precision prec (WD_F64: the plain FP64 solver) on a
  * non-zero right-hand side, L2 flushed before each timed solve -- and keeps the fastest
- * for the solvers of this precision and nrhs (wd_cg_solve, wd_cg_solve_canonical); the
- * plain operators keep wd_autotune's choice.  Uses and frees context scratch (256 MB for
- * the flush); synchronises the stream. */
+ * for the solvers of this precision and nrhs (wd_cg_solve, wd_cg_solve_canonical); with all
+ * extents even it tunes the even-odd solver's checkerboard kernels too, separately.  The
+ * plain operators keep wd_autotune's choice.  *site_tile / *rhs_tile: the choice for plain
+ * solves.  Uses and frees context scratch (256 MB for the flush); synchronises the stream. */
 wd_status wd_autotune_cg(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int *rhs_tile);
 /* Neighbour staging for the plain FP32 and FP16 operators (the paper's on-chip buffers
  * that feed the stencil pipeline, sections 6.3-6.4): with rows > 0, wd_apply,

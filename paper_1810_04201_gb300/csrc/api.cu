@@ -160,8 +160,8 @@ void graph_clear(wd_ctx *c) {
     c->graph_used.clear();
 }
 
-DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs) {
-    auto it = c->cg_tiles.find(p * 64 + nrhs);
+DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs, bool eo) {
+    auto it = c->cg_tiles.find(p * 64 + nrhs + (eo ? kEoTileKey : 0));
     return it != c->cg_tiles.end() ? it->second : tiles_for(c, p, nrhs);
 }
 

@@ -152,7 +152,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     if (rin != r64 && r64 != 18)
         return fail(c, WD_ERR_ARG, "wd_cg_solve: with compressed FP64 links the inner precision needs the same "
                                    "compression (see wd_set_link_compression)");
-    SolverPlan pl{r64, rin, kappa, nrhs, inner, cg_tiles_for(c, F64, nrhs), cg_tiles_for(c, inner, nrhs),
+    SolverPlan pl{r64, rin, kappa, nrhs, inner, cg_tiles_for(c, F64, nrhs, eo), cg_tiles_for(c, inner, nrhs, eo),
                   prm->normal_eq ? 1 : 0, eo ? 1 : 0};
     char key[256];
     snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, r64, rin, kappa, pl.t64.site_tile,
@@ -310,38 +310,48 @@ wd_status wd_autotune_cg(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int 
     prm.inner_prec = prec;
     prm.nrhs = nrhs;
     std::vector<wd_cg_result> res(nrhs);
-    const int key = (int)prec * 64 + nrhs;
     const int sts[] = {16, 32, 64, 128, 256};
     const int rts[] = {1, 2, 3, 4, 6, 8, 12, 16};
-    double best = 1e30;
-    DslashTiles bt = cg_tiles_for(c, (Prec)prec, nrhs);
+    bool even = true;
+    for (int mu = 0; mu < 4; ++mu) even &= c->g.L[mu] % 2 == 0;
     long long launches = 1;
-    for (int st : sts)
-        for (int rt : rts) {
-            if (rt > nrhs || st * rt > 256 || (st * rt) % 32 != 0) continue;
-            if (threads_per_site((Prec)prec) > 1 && st % 32 != 0) continue;
-            DslashTiles t;
-            t.site_tile = st;
-            t.rhs_tile = rt;
-            c->cg_tiles[key] = t;
-            double secs = 0.0;
-            for (int rep = 0; rep < 2; ++rep) {  // the first run builds and uploads the graph
-                WD_CUDA(c, cudaMemsetAsync(x, 0, fb, c->stream));
-                WD_CUDA(c, cudaMemsetAsync(flush, rep, flush_bytes, c->stream));
-                s = wd_cg_solve(c, 0.12, b, x, &prm, res.data());
-                if (s != WD_OK && s != WD_ERR_NOT_CONVERGED) {
-                    c->cg_tiles[key] = bt;
-                    return s;
+    DslashTiles chosen{};
+    // plain solves, then (all extents even) even-odd solves, whose checkerboard kernels
+    // may prefer another shape
+    for (int pc = 0; pc < (even ? 2 : 1); ++pc) {
+        prm.precondition = pc;
+        const int key = (int)prec * 64 + nrhs + (pc ? kEoTileKey : 0);
+        double best = 1e30;
+        DslashTiles bt = cg_tiles_for(c, (Prec)prec, nrhs, pc != 0);
+        for (int st : sts)
+            for (int rt : rts) {
+                if (rt > nrhs || st * rt > 256 || (st * rt) % 32 != 0) continue;
+                if (threads_per_site((Prec)prec) > 1 && st % 32 != 0) continue;
+                DslashTiles t;
+                t.site_tile = st;
+                t.rhs_tile = rt;
+                c->cg_tiles[key] = t;
+                double secs = 0.0;
+                for (int rep = 0; rep < 2; ++rep) {  // the first run builds and uploads the graph
+                    WD_CUDA(c, cudaMemsetAsync(x, 0, fb, c->stream));
+                    WD_CUDA(c, cudaMemsetAsync(flush, rep, flush_bytes, c->stream));
+                    s = wd_cg_solve(c, 0.12, b, x, &prm, res.data());
+                    if (s != WD_OK && s != WD_ERR_NOT_CONVERGED) {
+                        c->cg_tiles[key] = bt;
+                        return s;
+                    }
+                    launches += c->launches;
+                    secs = res[0].seconds;
                 }
-                launches += c->launches;
-                secs = res[0].seconds;
+                if (secs < best) {
+                    best = secs;
+                    bt = t;
+                }
             }
-            if (secs < best) {
-                best = secs;
-                bt = t;
-            }
-        }
-    c->cg_tiles[key] = bt;
+        c->cg_tiles[key] = bt;
+        if (pc == 0) chosen = bt;
+    }
+    const DslashTiles bt = chosen;
     ws_release(c, "tunecg_flush");
     ws_release(c, "tunecg_b");
     ws_release(c, "tunecg_x");

@@ -17,7 +17,10 @@
 // Thread 0 issues the copies and waits on the mbarriers; a block-wide barrier then hands
 // the stage to all threads and, after the tile, hands it back.  Every wait is bounded:
 // when one runs out the kernel sets the context's error word, waits (bounded) for the
-// copies it still has in flight, and returns.
+// copies it still has in flight, and returns.  With WD_STAGED_STALL_TEST=1 in the
+// environment, block 0 first waits on an mbarrier that nothing completes: the test of
+// that path, which faults nothing.
+#include <cstdlib>
 #include "dslash.cuh"
 #include "wd_host.h"
 
@@ -37,7 +40,8 @@ struct StagedArgs {
     int stages;
     unsigned stage_bytes;
     unsigned *err;         // 1 when a wait ran out
-    long long spin_limit;  // try_wait calls before giving up
+    long long spin_limit;  // SM clock cycles a wait may take before it gives up
+    int stall_test;        // block 0 first waits on a barrier that nothing completes
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -66,11 +70,13 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// bounded wait for phase `parity` of bar
+// wait for phase `parity` of bar, for at most limit SM clock cycles (try_wait may suspend
+// the thread for a time of its own choosing, so the bound is on the clock, not on calls)
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
-    for (long long k = 0; k < limit; ++k)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
 }
 
 // layout of one stage: per component array j (FP32: 6 float4, FP16: 3 uint4), the seven
@@ -189,12 +195,13 @@ __device__ __forceinline__ void staged_dir(const StagedArgs &a, const TileRanges
 template <int P, int RECON, bool DAG>
 __global__ void __launch_bounds__(256) dslash_staged_kernel(StagedArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ unsigned long long full[4];
+    __shared__ unsigned long long full[4], never;
     __shared__ int abort_flag;
     const int T = a.rows * a.g.L[0];
     const int total = a.tiles * a.nrhs;
     if (threadIdx.x == 0) {
         for (int k = 0; k < a.stages; ++k) mbar_init(&full[k], 1);
+        mbar_init(&never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
         for (int k = 0; k < a.stages; ++k) {
@@ -208,11 +215,13 @@ __global__ void __launch_bounds__(256) dslash_staged_kernel(StagedArgs a) {
         const int stage = k % a.stages;
         const unsigned parity = (unsigned)(k / a.stages) & 1u;
         unsigned char *buf = smem + (size_t)stage * a.stage_bytes;
-        if (threadIdx.x == 0 && !mbar_wait(&full[stage], parity, a.spin_limit)) {
+        const bool stalled = a.stall_test && k == 0 && blockIdx.x == 0;
+        if (threadIdx.x == 0 && ((stalled && !mbar_wait(&never, 0, a.spin_limit)) ||
+                                 !mbar_wait(&full[stage], parity, a.spin_limit))) {
             atomicExch(a.err, 1u);
             abort_flag = 1;
             // the copies still in flight land in this block's shared memory: let them finish
-            for (int j = 1; j < a.stages; ++j) {
+            for (int j = 0; j < a.stages; ++j) {
                 const int kk = k + j;
                 if (blockIdx.x + kk * gridDim.x < total)
                     mbar_wait(&full[kk % a.stages], (unsigned)(kk / a.stages) & 1u, a.spin_limit);
@@ -304,7 +313,9 @@ cudaError_t launch_apply_staged(const DslashArgs &d, Prec p, int recon, bool dag
     a.stages = stages;
     a.stage_bytes = staged_stage_bytes(p, d.g, rows);
     a.err = err;
-    a.spin_limit = 1ll << 24;  // try_wait calls: of the order of a second or more in all
+    const char *stall = getenv("WD_STAGED_STALL_TEST");
+    a.stall_test = stall && stall[0] == '1';
+    a.spin_limit = a.stall_test ? 200000000ll : 2000000000ll;  // about 0.1 s / 1 s at GB300 clocks
     return with_recon(recon, [&](auto rc) {
         constexpr int R = decltype(rc)::value;
         if (p == F32) return dagger ? go_staged<F32, R, true>(a, st) : go_staged<F32, R, false>(a, st);

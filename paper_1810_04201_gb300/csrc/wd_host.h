@@ -79,8 +79,10 @@ wd_status gauge_get_eo(wd_ctx *c, Prec p, const void **out, size_t *dir_bytes);
 Geom eo_geom(const wd_ctx *c, int parity);
 
 DslashTiles tiles_for(wd_ctx *c, Prec p, int nrhs);
-// launch shape of the solvers' fused Dslash kernels: wd_autotune_cg's choice, else tiles_for
-DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs);
+// launch shape of the solvers' fused Dslash kernels, for plain or even-odd solves:
+// wd_autotune_cg's choice, else tiles_for
+constexpr int kEoTileKey = 1024;
+DslashTiles cg_tiles_for(wd_ctx *c, Prec p, int nrhs, bool eo);
 // frees a workspace buffer (no-op when absent)
 void ws_release(wd_ctx *c, const std::string &name);
 

@@ -298,3 +298,24 @@ def test_rhs_per_thread_matches_oracle(wd, nrhs, site_tile, rhs_tile, k):
             assert oracle.rel_err(outs[k, dag], outs[1, dag]) < 1e-7
     with pytest.raises(wd.WDError):
         lat.set_rhs_per_thread(0, nrhs, 2)  # FP64: one right-hand side per thread
+
+
+def test_staged_wait_timeout_is_reported(wd, monkeypatch):
+    """A wait of the staged kernel that runs out (block 0 waits on an mbarrier that nothing
+    completes) sets the context's staging error word instead of hanging; the block drains its
+    copies in flight and leaves, and the context stays usable."""
+    dims = (8, 4, 4, 6)
+    U = gen.haar_links(dims, seed=97)
+    psi = gen.gaussian_source(dims, seed=98)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    f = lat.pack(psi, 1)
+    lat.set_staging(1, 2, 2)
+    monkeypatch.setenv("WD_STAGED_STALL_TEST", "1")
+    lat.apply(0.12, f, lat.new_field(1), 1)
+    assert lat.staging_error() == 1
+    monkeypatch.delenv("WD_STAGED_STALL_TEST")
+    o = lat.new_field(1)
+    lat.apply(0.12, f, o, 1)
+    assert lat.staging_error() == 0
+    assert oracle.rel_err(lat.unpack(o, 1), oracle.apply_D(U, psi, 0.12, dims)) < TOL[1]
