@@ -364,6 +364,8 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f16", "df32"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="with --dslash-only: autotune the launch shape first")
+    ap.add_argument("--prefetch", action="store_true",
+                    help="with --dslash-only: the FP32 kernel that prefetches neighbour spinors by cp.async")
     ap.add_argument("--tiles", default=None, metavar="ST,RT[,K]",
                     help="with --dslash-only: fix the launch shape (site tile, RHS tile, RHS per thread)")
     ap.add_argument("--staged", default=None, metavar="R,S[;R,S...]",
@@ -887,6 +889,9 @@ def dslash_only(args):
         if len(t) > 2:
             lat.set_rhs_per_thread(pid, args.nrhs, t[2])
         tuned = list(lat.tiles(pid, args.nrhs))
+    if args.prefetch:
+        lat.set_prefetch(pid, True)
+        tuned = {"tiles": list(lat.tiles(pid, args.nrhs)), "prefetch": True}
     fi = lat.pack(b if args.nrhs > 1 else b[0], pid)
     fo = lat.new_field(pid, args.nrhs)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")

@@ -196,7 +196,10 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
  *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
  *              1: block CG (one Krylov space for all right-hand sides, FP64 only)
- *   rhs_tile   right-hand sides per thread block in the multi-RHS Dslash (0 = tuned)
+ *   rhs_tile   right-hand sides per thread block in the solver's multi-RHS Dslash
+ *              kernels (0 = the tuned shape; otherwise the tuned site tile, halved
+ *              while site tile x rhs_tile exceeds 256; WD_ERR_ARG if that leaves no
+ *              block of a multiple of 32 threads)
  *   normal_eq  0: CGNR, D^dag D x = D^dag b (default).  1: CGNE, the form of the
  *              paper's listing (section 2.2): D D^dag y = b from y = 0, then
  *              x = D^dag y; the iterated residual is b - D x itself, tol applies
@@ -208,8 +211,8 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *              kappa H_eo b_o, solved by CGNR on that operator, with x_o = b_o +
  *              kappa H_oe x_e afterwards.  The reduced system is solved to tol / 2
  *              and resumed from its solution with a tighter tolerance (at most three
- *              times) until the recomputed FP64 residual of D x = b on the whole
- *              lattice meets tol; iterations are summed.  Needs even extents; CGNR
+ *              times) until the residual stop_rule names, recomputed in FP64 on the
+ *              whole lattice, meets tol; iterations are summed.  Needs even extents; CGNR
  *              only (not with block or normal_eq).
  *   stop_rule  WD_STOP_NORMAL (default): tol applies to the normal-equation residual,
  *              ||D^dag(b - D x)|| <= tol ||D^dag b||.  WD_STOP_SYSTEM: tol applies to the
@@ -307,6 +310,13 @@ wd_status wd_autotune_cg(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, in
  * checkerboard).  Unsupported shapes: WD_ERR_ARG.  No counterpart in the paper beyond the
  * buffers it mirrors. */
 wd_status wd_set_staging(wd_ctx *ctx, wd_prec prec, int rows, int stages);
+/* Per-thread prefetch for the plain FP32 operator (on = 1): each thread copies the neighbour
+ * spinors of its next two hops into its own slots of shared memory with cp.async while it
+ * computes the current hop, so more loads are in flight at the same occupancy; links are read
+ * directly.  Same launch shapes as the direct kernel (one right-hand side per thread).  No
+ * counterpart in the paper beyond the on-chip buffers of sections 6.3-6.4.  on = 0 (default):
+ * the direct-load kernel.  Other precisions, split or checkerboard lattices: WD_ERR_ARG. */
+wd_status wd_set_prefetch(wd_ctx *ctx, wd_prec prec, int on);
 /* The staged kernel bounds its waits; one that ran out since the last call sets *err to 1
  * (and that launch's output is incomplete).  Synchronises the stream and clears the word. */
 wd_status wd_staging_error(wd_ctx *ctx, unsigned *err);

@@ -432,7 +432,11 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
     a.gauge_dir = gauge_dir_bytes(c, (Prec)prec);
     a.kappa = kappa;
     a.nrhs = nrhs;
-    if (c->staged_rows[prec]) {
+    if (c->prefetch[prec] && prec == WD_F32) {
+        DslashTiles t = tiles_for(c, F32, nrhs);
+        t.rhs_per_thread = 1;
+        WD_CUDA(c, launch_apply_prefetch(a, link_recon(c, F32), dagger, t, c->stream));
+    } else if (c->staged_rows[prec]) {
         void *err;
         if ((s = ws_get(c, "staged_err", sizeof(unsigned), &err)) != WD_OK) return s;
         WD_CUDA(c, launch_apply_staged(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, c->staged_rows[prec],

@@ -154,6 +154,19 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
                                    "compression (see wd_set_link_compression)");
     SolverPlan pl{r64, rin, kappa, nrhs, inner, cg_tiles_for(c, F64, nrhs, eo), cg_tiles_for(c, inner, nrhs, eo),
                   prm->normal_eq ? 1 : 0, eo ? 1 : 0};
+    if (prm->rhs_tile > 0) {
+        // a fixed right-hand-side tile for the fused kernels, with the tuned site tile
+        // shrunk where site_tile x rhs_tile would pass 256 threads
+        const int rt = prm->rhs_tile < nrhs ? prm->rhs_tile : nrhs;
+        for (DslashTiles *t : {&pl.t64, &pl.tin}) {
+            t->rhs_tile = rt;
+            t->rhs_per_thread = 1;
+            while (t->site_tile > 32 && t->site_tile * rt > 256) t->site_tile /= 2;
+            if (t->site_tile * rt > 256 || (t->site_tile * rt) % 32 != 0)
+                return fail(c, WD_ERR_ARG, "wd_cg_solve: rhs_tile gives no launch shape of at most 256 threads, a "
+                                           "multiple of 32");
+        }
+    }
     char key[256];
     snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, r64, rin, kappa, pl.t64.site_tile,
              pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo);

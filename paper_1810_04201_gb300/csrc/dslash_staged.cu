@@ -260,6 +260,121 @@ __global__ void __launch_bounds__(256) dslash_staged_kernel(StagedArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- per-thread prefetch
+// The FP32 operator with each thread (one site, one right-hand side) copying the neighbour
+// spinors of its next hops into a private ring of shared-memory slots with cp.async (16-byte
+// global -> shared copies that hold no register), `kRing` - 1 hops ahead of the one it
+// computes; the links are read directly.  Occupancy stays that of the direct kernel (288
+// bytes of shared memory per thread), while every thread keeps two more hops of spinor
+// loads in flight.  Slots are [slot][component][thread]: a warp's copies and reads of one
+// component are 512 contiguous bytes, free of bank conflicts.
+constexpr int kRing = 3;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// global site of hop h (mu = h / 2, forward for even h) of site s with coordinates xc
+__device__ __forceinline__ int hop_site(const Geom &g, int s, const int (&xc)[4], int h) {
+    const int mu = h >> 1, L = g.L[mu], st = g.stride[mu], c = xc[mu];
+    if ((h & 1) == 0) return c == L - 1 ? s - (L - 1) * st : s + st;
+    return c == 0 ? s + (L - 1) * st : s - st;
+}
+
+__device__ __forceinline__ void prefetch_spinor(float4 *ring, int slot, int nthr, int tid, const void *in, int Vs,
+                                                int site) {
+    const float4 *src = reinterpret_cast<const float4 *>(in) + site;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) cp_async16(ring + ((size_t)slot * 6 + j) * nthr + tid, src + (size_t)j * Vs);
+}
+
+template <int RECON, bool DAG, int H>
+__device__ __forceinline__ void pipe_hop(const DslashArgs &a, const float4 *ring, int nthr, int tid, int s,
+                                         const int (&xc)[4], int nb, C<float> (&acc)[12]) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = FWD ? SF : -SF;
+    const Geom &g = a.g;
+    C<float> p[12], h[6], w[6], u[9];
+    const float4 *slot = ring + (size_t)(H % kRing) * 6 * nthr + tid;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float4 t = slot[(size_t)j * nthr];
+        p[2 * j] = C<float>{t.x, t.y};
+        p[2 * j + 1] = C<float>{t.z, t.w};
+    }
+    project<MU, S>(p, h);
+    const char *gdir = reinterpret_cast<const char *>(a.gauge) + (size_t)MU * a.gauge_dir;
+    LinkIO<F32, RECON>::load(gdir, g.Vs, FWD ? s : nb, u);
+    const int c = xc[MU];
+    const bool flip = MU == 3 && g.antiperiodic && (FWD ? c == g.L[3] - 1 : c == 0);
+    su3_mult<!FWD>(u, h, w, flip);
+    accumulate<MU, S>(acc, w);
+}
+
+template <int RECON, bool DAG>
+__global__ void __launch_bounds__(256, 3) dslash_pipe_kernel(DslashArgs a) {
+    extern __shared__ __align__(16) float4 ring[];
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int r = tile_y() * blockDim.y + threadIdx.y;
+    if (r >= a.nrhs) return;  // no block-wide step follows
+    const void *in = rhs_ptr<float>(a.in, a.in_stride, r);
+    for (int s0 = tile_x() * blockDim.x; s0 < a.g.V; s0 += gridDim.x * blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        if (s >= a.g.V) continue;
+        int xc[4], rem = s;
+        xc[0] = rem % a.g.L[0]; rem /= a.g.L[0];
+        xc[1] = rem % a.g.L[1]; rem /= a.g.L[1];
+        xc[2] = rem % a.g.L[2];
+        xc[3] = rem / a.g.L[2];
+        // the first kRing - 1 hops in flight, then one more per hop computed
+#pragma unroll
+        for (int hh = 0; hh < kRing - 1; ++hh) {
+            prefetch_spinor(ring, hh % kRing, nthr, tid, in, a.g.Vs, hop_site(a.g, s, xc, hh));
+            cp_async_commit();
+        }
+        C<float> acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = C<float>{0.f, 0.f};
+#define WD_PIPE_STEP(H)                                                                        \
+        if (H + kRing - 1 < 8)                                                                 \
+            prefetch_spinor(ring, (H + kRing - 1) % kRing, nthr, tid, in, a.g.Vs,              \
+                            hop_site(a.g, s, xc, (H + kRing - 1) & 7));                        \
+        cp_async_commit();                                                                     \
+        cp_async_wait<kRing - 1>();                                                            \
+        pipe_hop<RECON, DAG, H>(a, ring, nthr, tid, s, xc, hop_site(a.g, s, xc, H), acc);
+        WD_PIPE_STEP(0) WD_PIPE_STEP(1) WD_PIPE_STEP(2) WD_PIPE_STEP(3)
+        WD_PIPE_STEP(4) WD_PIPE_STEP(5) WD_PIPE_STEP(6) WD_PIPE_STEP(7)
+#undef WD_PIPE_STEP
+        C<float> p[12];
+        SpinorIO<F32>::load(a.xsrc ? rhs_ptr<float>(a.xsrc, a.xsrc_stride, r) : in, a.g.Vs, s, p);
+        const float kap = (float)a.kappa;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[c] = C<float>{p[c].re - kap * acc[c].re, p[c].im - kap * acc[c].im};
+        SpinorIO<F32>::store(rhs_ptr<float>(a.out, a.out_stride, r), a.g.Vs, s, p);
+    }
+}
+
+cudaError_t launch_apply_prefetch(const DslashArgs &a, int recon, bool dagger, DslashTiles t, cudaStream_t st) {
+    const dim3 block(t.site_tile, t.rhs_tile);
+    const dim3 grid(site_blocks<F32>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
+    const size_t smem = (size_t)kRing * 6 * 16 * block.x * block.y;
+    return with_recon(recon, [&](auto rc) {
+        constexpr int R = decltype(rc)::value;
+        auto k = dagger ? dslash_pipe_kernel<R, true> : dslash_pipe_kernel<R, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, block, smem, st>>>(a);
+        return cudaGetLastError();
+    });
+}
+
 // bytes of one stage: (5 T + 2 Lx) sites of every component array (and the FP16 scales)
 inline unsigned staged_stage_bytes(Prec p, const Geom &g, int rows) {
     const size_t S = (size_t)5 * rows * g.L[0] + 2 * (size_t)g.L[0];
@@ -341,6 +456,16 @@ wd_status wd_set_staging(wd_ctx *c, wd_prec prec, int rows, int stages) {
                                    "a multiple of 4), 2 to 4 stages within 227 KB of shared memory, a full lattice");
     c->staged_rows[prec] = rows;
     c->staged_stages[prec] = stages;
+    return WD_OK;
+}
+
+wd_status wd_set_prefetch(wd_ctx *c, wd_prec prec, int on) {
+    if (!c) return WD_ERR_ARG;
+    if ((int)prec < 0 || (int)prec >= kNumPrec) return fail(c, WD_ERR_ARG, "wd_set_prefetch: bad precision");
+    if (on && prec != WD_F32) return fail(c, WD_ERR_ARG, "wd_set_prefetch: the FP32 operator only");
+    if (on && (c->g.eo_parity >= 0 || c->g.split_t))
+        return fail(c, WD_ERR_ARG, "wd_set_prefetch: full, unsplit lattices only");
+    c->prefetch[prec] = on != 0;
     return WD_OK;
 }
 

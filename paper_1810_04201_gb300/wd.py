@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "wd_get_tiles": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "wd_set_rhs_per_thread": ([P, I, I, I], I),
         "wd_staging_error": ([P, ctypes.POINTER(ctypes.c_uint)], I),
+        "wd_set_prefetch": ([P, I, I], I),
         "wd_kernel_launches": ([P], ctypes.c_longlong),
         "wd_measure_fp64_rate": ([ctypes.POINTER(D)], I),
         "wd_create_split": ([ctypes.POINTER(P), ctypes.POINTER(I), I, I, I, P], I),
@@ -322,6 +323,10 @@ class Lattice:
         """Plain operators of precision prec through the staged kernel (rows > 0) or the
         direct-load one (rows = 0)."""
         self._check(self.lib.wd_set_staging(self.ctx, prec, int(rows), int(stages)), "wd_set_staging")
+
+    def set_prefetch(self, prec, on=True):
+        """The plain FP32 operator through the cp.async-prefetch kernel (on) or the direct one."""
+        self._check(self.lib.wd_set_prefetch(self.ctx, prec, int(bool(on))), "wd_set_prefetch")
 
     def staging_error(self) -> int:
         w = ctypes.c_uint()

@@ -568,3 +568,25 @@ def test_autotune_cg_keeps_solutions(wd, inner, nrhs):
     for j in range(nrhs):
         x_ref, _ = ref_solution(U, B[j], kappa, dims)
         assert oracle.rel_err(X[j], x_ref) < 1e-9
+
+
+def test_fixed_rhs_tile_in_solver(wd):
+    """params.rhs_tile fixes the right-hand-side tile of the solver's kernels: same solutions."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = gen.haar_links(dims, seed=85)
+    B = gen.gaussian_source(dims, seed=86, nrhs=5)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U)
+    fb = lat.pack(B)
+    xs = {}
+    for rt in (0, 1, 2, 5):
+        fx = lat.new_field(nrhs=5)
+        p = lat.params(tol=1e-10, nrhs=5, rhs_tile=rt, inner=1)
+        res = (wd.CGResult * 5)()
+        import ctypes
+        st = lat.lib.wd_cg_solve(lat.ctx, kappa, ctypes.c_void_p(fb.data_ptr()), ctypes.c_void_p(fx.data_ptr()),
+                                 ctypes.byref(p), res)
+        assert st == 0 and all(r.true_rel_resid <= 1e-10 for r in res)
+        xs[rt] = lat.unpack(fx, nrhs=5, squeeze=False)
+    for rt in (1, 2, 5):
+        assert oracle.rel_err(xs[rt], xs[0]) < 1e-9

@@ -319,3 +319,28 @@ def test_staged_wait_timeout_is_reported(wd, monkeypatch):
     lat.apply(0.12, f, o, 1)
     assert lat.staging_error() == 0
     assert oracle.rel_err(lat.unpack(o, 1), oracle.apply_D(U, psi, 0.12, dims)) < TOL[1]
+
+
+@pytest.mark.parametrize("dims,nrhs", [((8, 4, 6, 6), 1), ((6, 4, 4, 6), 3), ((5, 3, 4, 6), 2)])
+def test_prefetch_dslash_matches_oracle(wd, dims, nrhs):
+    """The FP32 kernel with per-thread cp.async prefetch of the neighbour spinors: D and D^dag,
+    recon 18/12/8, against the oracle and the direct kernel."""
+    U = gen.haar_links(dims, seed=99)
+    psi = gen.gaussian_source(dims, seed=100, nrhs=nrhs)
+    for recon in (18, 12, 8):
+        lat = wd.Lattice(dims)
+        lat.set_gauge(U, recon=recon)
+        f = lat.pack(psi if nrhs > 1 else psi[0], 1)
+        for dag in (False, True):
+            outs = []
+            for on in (False, True):
+                lat.set_prefetch(1, on)
+                o = lat.new_field(1, nrhs=nrhs)
+                lat.apply(0.12, f, o, 1, nrhs=nrhs, dagger=dag)
+                outs.append(lat.unpack(o, 1, nrhs=nrhs, squeeze=False))
+            for j in range(nrhs):
+                want = oracle.apply_D(U, psi[j], 0.12, dims, dagger=dag)
+                assert oracle.rel_err(outs[1][j], want) < TOL[1], (recon, dag, j)
+            assert oracle.rel_err(outs[1], outs[0]) < 1e-7
+    with pytest.raises(wd.WDError):
+        lat.set_prefetch(0, True)
