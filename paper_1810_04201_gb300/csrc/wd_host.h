@@ -5,6 +5,7 @@
 #include <type_traits>
 #include <nvtx3/nvToolsExt.h>
 #include "wd_internal.cuh"
+#include "wd_ctx.h"
 
 namespace wd {
 
