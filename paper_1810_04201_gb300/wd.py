@@ -460,7 +460,9 @@ def _cuda_bytes(ptr, n):
 class DistComm:
     """wd_comm over torch.distributed for split solves spread over processes (one
     sub-lattice block per process): faces through TSplit.exchange, sums through all_reduce.
-    Keeps its ctypes callbacks alive while it exists."""
+    With NCCL the faces go device to device; with gloo (which sends host tensors) they are
+    staged through host memory on the library's work stream, which must be torch's current
+    stream (the default for SplitLattice).  Keeps its ctypes callbacks alive while it exists."""
 
     def __init__(self, dist, split: TSplit, first_rank, last_rank, proc_of_rank, group=None):
         self.dist, self.split, self.group = dist, split, group
@@ -472,7 +474,13 @@ class DistComm:
         def exchange(user, send_prev, recv_prev, send_next, recv_next, nbytes, stream):
             try:
                 t = [_cuda_bytes(p, nbytes) for p in (send_prev, recv_prev, send_next, recv_next)]
-                TSplit.exchange(self.dist, self.me, self.prev, self.next, t[0], t[1], t[2], t[3], self.group)
+                if self.dist.get_backend(self.group) == "nccl":
+                    TSplit.exchange(self.dist, self.me, self.prev, self.next, t[0], t[1], t[2], t[3], self.group)
+                else:
+                    h = [x.cpu() for x in t]  # waits for the packed faces on the current stream
+                    TSplit.exchange(self.dist, self.me, self.prev, self.next, h[0], h[1], h[2], h[3], self.group)
+                    t[1].copy_(h[1])
+                    t[3].copy_(h[3])
                 return 0
             except Exception:  # a failed exchange is reported through the status, never raised through C
                 return 1

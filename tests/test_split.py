@@ -3,7 +3,8 @@ neighbours' boundary sites, global scalar products in CG).
 
 GPU (one device, all sub-lattices in one process): the split operator -- faces packed,
 exchanged by device copies, interior and face launches -- against the oracle's unsplit D
-and D^dag; the decomposed CG against the oracle's solution.
+and D^dag; the decomposed CG against the oracle's solution.  GPU, two processes sharing the
+device: the decomposed CG with the faces and sums through DistComm's callbacks over gloo.
 
 CPU (world_size-2 gloo ranks): the host-side logic of the split -- which slices each rank
 owns, who its neighbours are, the face exchange in both directions, the sign of the global
@@ -251,3 +252,63 @@ def test_split_refusals(wd):
     plain = wd.Lattice(dims)
     plain.set_gauge(U)
     assert int(lib.wd_face_bytes(plain.ctx, 0, 1)) == 0
+
+
+def _split_solve_rank(rank, world, port, dims, kappa, out):
+    """One process of a two-process split solve on one GPU: its own sub-lattice and context,
+    faces and scalar products through DistComm over gloo (host-staged faces)."""
+    import datetime
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
+    try:
+        import __graft_entry__  # noqa: F401  (puts the repository on the path)
+        from paper_1810_04201_gb300 import wd
+        torch.cuda.set_device(0)
+        U = gen.haar_links(dims, seed=75)
+        b = gen.gaussian_source(dims, seed=76)
+        lat = wd.SplitLattice(dims, world, rank)
+        lat.set_gauge(lat.split.local_links(U, rank))
+        fb = lat.pack(lat.split.local_field(b, rank))
+        fx = lat.new_field()
+        comm = wd.DistComm(dist, lat.split, rank, rank, lambda k: k)
+        res, st = wd.cg_split([lat], kappa, [fb], [fx], tol=1e-10, comm=comm)
+        out.put((rank, st, res, lat.unpack(fx)))
+    except Exception as e:  # reported to the parent, which fails the test
+        out.put((rank, -1, repr(e), None))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_split_cg_two_processes_gloo(wd):
+    """The decomposed CG across two processes sharing one GPU: each process holds one sub-lattice,
+    the library calls DistComm's callbacks for the face exchange and the global sums (gloo, faces
+    staged through host memory; no kernel waits on the other process), and the joined solution is
+    the oracle's, with the iteration count of the one-process split solve."""
+    dims, kappa = (6, 4, 6, 8), 0.12
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_solve_rank, args=(r, 2, port, dims, kappa, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict((r[0], r[1:]) for r in (q.get(timeout=300) for _ in range(2)))
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+        assert p.exitcode == 0
+    for rank in (0, 1):
+        assert got[rank][0] == 0, got[rank]
+    x = np.concatenate([got[0][2], got[1][2]])
+    U = gen.haar_links(dims, seed=75)
+    b = gen.gaussian_source(dims, seed=76)
+    x_ref, _ = oracle.cgnr(U, b, kappa, dims, tol=1e-13)
+    assert oracle.rel_err(x, x_ref) < 1e-9
+    assert got[0][1]["iters"] == got[1][1]["iters"]
+    assert got[0][1]["true_rel_resid"] == pytest.approx(got[1][1]["true_rel_resid"], rel=1e-12)
+    blocks = split_blocks(wd, dims, 2, U)
+    res1, st1 = wd.cg_split(blocks, kappa, [blk.pack(blk.split.local_field(b, r)) for r, blk in enumerate(blocks)],
+                            [blk.new_field() for blk in blocks], tol=1e-10)
+    assert st1 == 0 and abs(res1["iters"] - got[0][1]["iters"]) <= 1
