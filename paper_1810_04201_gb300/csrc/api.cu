@@ -194,6 +194,7 @@ wd_ctx::~wd_ctx() {
     }
     if (gauge_canon) cudaFree(gauge_canon);
     if (g.dbg) cudaFree(g.dbg);
+    if (staged_err) cudaFree(staged_err);
 }
 
 static bool bad_prec(int p) { return p < 0 || p >= kNumPrec; }
@@ -437,10 +438,9 @@ static wd_status apply_common(wd_ctx *c, double kappa, const void *in, void *out
         t.rhs_per_thread = 1;
         WD_CUDA(c, launch_apply_prefetch(a, link_recon(c, F32), dagger, t, c->stream));
     } else if (c->staged_rows[prec]) {
-        void *err;
-        if ((s = ws_get(c, "staged_err", sizeof(unsigned), &err)) != WD_OK) return s;
+        if ((s = staged_error_word(c)) != WD_OK) return s;
         WD_CUDA(c, launch_apply_staged(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, c->staged_rows[prec],
-                                       c->staged_stages[prec], static_cast<unsigned *>(err), c->stream));
+                                       c->staged_stages[prec], c->staged_err, c->stream));
     } else {
         WD_CUDA(c, launch_apply(a, (Prec)prec, link_recon(c, (Prec)prec), dagger, tiles_for(c, (Prec)prec, nrhs),
                                 c->stream));

@@ -33,6 +33,11 @@ namespace wd {
 constexpr int kTile = 128;
 constexpr int kHalfTile = kTile / 2;  // sites of one pass of the two-lane FP64 phases
 constexpr int kPart = 4;              // partial sums per tile
+// A reliable update that delta triggers waits up to this many iterations, while the
+// lattice's CG steps go on, so that the updates of many lattices share one update phase
+// (three grid barriers and a walk over every tile).  Convergence and the iteration limit
+// still update at once.
+constexpr int kDeferIters = 4;
 
 struct LatDesc {
     Geom g;
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
     auto all = [](const Scalars &, int) { return 1; };
     auto active = [](const Scalars &c, int) { return c.active; };
-    auto updating = [](const Scalars &c, int) { return c.active && c.do_update; };
+    auto updating = [](const Scalars &c, int) { return c.active && (c.do_update || c.pending); };
     auto x0_nonzero = [&](const Scalars &, int l) { return a.lstate[2 * l]; };
     auto unchecked = [&](const Scalars &, int l) { return 1 - a.lstate[2 * l + 1]; };
 
@@ -345,13 +350,19 @@ __global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
                 const double rn = t[0];
                 c.iter += 1;
                 if (!isfinite(rn)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
-                if (rn <= c.tol2 || rn < c.delta2 * c.rmax2 || c.iter >= c.max_iter) {
+                if (rn <= c.tol2 || c.iter >= c.max_iter) {
+                    // stopping: update now, in place of this step
                     c.do_update = 1;
                     atomicExch(a.flags + 1, 1);
                 } else {
                     c.beta = rn / c.rho;
                     c.rho = rn;
                     c.rmax2 = fmax(c.rmax2, rn);
+                    if (!c.pending && rn < c.delta2 * c.rmax2) {
+                        c.pending = 1;
+                        c.pending_since = c.iter;
+                    }
+                    if (c.pending && c.iter - c.pending_since >= kDeferIters) atomicExch(a.flags + 1, 1);
                 }
             });
         });
@@ -419,7 +430,9 @@ __global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
                     const double rt = t[0];
                     c.reliable += 1;
                     if (!isfinite(rt)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
-                    c.beta = rt / c.rho;
+                    // beta = |r_true|^2 / |r|^2 of the previous step; a deferred update comes after
+                    // this iteration's step, which set beta = rho / rho_prev and rho = |r|^2
+                    c.beta = c.do_update ? rt / c.rho : rt * c.beta / c.rho;
                     c.rho = rt;
                     c.rmax2 = rt;
                     if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
@@ -439,7 +452,7 @@ __global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
             const Scalars &c = a.sc[l];
             const RS beta = RS(c.beta);
             C<RS> w[12], p[12];
-            if (c.do_update) {
+            if (c.do_update || (c.pending && *(volatile int *)(a.flags + 1))) {
                 C<double> d[12];
                 SpinorIO<F64>::template load<false>(L.r, L.g.Vs, s, d);
 #pragma unroll
@@ -456,7 +469,12 @@ __global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
         if (!grid_barrier(a)) return;
         // clear the pending flags (one block owns them), then a barrier before the next step
         if (blockIdx.x == 0) {
-            for (int l = threadIdx.x; l < a.nlat; l += blockDim.x) a.sc[l].do_update = 0;
+            const bool updated = *(volatile int *)(a.flags + 1) != 0;
+            __syncthreads();  // every thread has read the flag before thread 0 clears it
+            for (int l = threadIdx.x; l < a.nlat; l += blockDim.x) {
+                a.sc[l].do_update = 0;
+                if (updated) a.sc[l].pending = 0;
+            }
             if (threadIdx.x == 0) a.flags[1] = 0;
         }
         if (!grid_barrier(a)) return;

@@ -442,6 +442,17 @@ cudaError_t launch_apply_staged(const DslashArgs &d, Prec p, int recon, bool dag
 
 using namespace wd;
 
+namespace wd {
+wd_status staged_error_word(wd_ctx *c) {
+    if (c->staged_err) return WD_OK;
+    void *p = nullptr;
+    WD_CUDA(c, cudaMalloc(&p, sizeof(unsigned)));
+    c->staged_err = static_cast<unsigned *>(p);
+    WD_CUDA(c, cudaMemsetAsync(c->staged_err, 0, sizeof(unsigned), c->stream));
+    return WD_OK;
+}
+}  // namespace wd
+
 extern "C" {
 
 wd_status wd_set_staging(wd_ctx *c, wd_prec prec, int rows, int stages) {
@@ -472,12 +483,11 @@ wd_status wd_set_prefetch(wd_ctx *c, wd_prec prec, int on) {
 wd_status wd_staging_error(wd_ctx *c, unsigned *err) {
     if (!c || !err) return WD_ERR_ARG;
     *err = 0;
-    void *w;
-    wd_status s = ws_get(c, "staged_err", sizeof(unsigned), &w);
+    wd_status s = staged_error_word(c);
     if (s != WD_OK) return s;
     WD_CUDA(c, cudaStreamSynchronize(c->stream));
-    WD_CUDA(c, cudaMemcpy(err, w, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    WD_CUDA(c, cudaMemset(w, 0, sizeof(unsigned)));
+    WD_CUDA(c, cudaMemcpy(err, c->staged_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    WD_CUDA(c, cudaMemset(c->staged_err, 0, sizeof(unsigned)));
     return WD_OK;
 }
 

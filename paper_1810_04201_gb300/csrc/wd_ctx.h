@@ -31,6 +31,7 @@ struct wd_ctx {
     std::map<int, wd::DslashTiles> cg_tiles;           // the solvers' fused kernels (wd_autotune_cg); same key
     int staged_rows[wd::kNumPrec] = {};                // plain operators through the staged kernel (0: off)
     bool prefetch[wd::kNumPrec] = {};                  // plain FP32 operator through the cp.async-prefetch kernel
+    unsigned *staged_err = nullptr;                    // the staged kernel's error word (zeroed when allocated)
     int staged_stages[wd::kNumPrec] = {};
     void *noalloc_scratch = nullptr;                   // device address of the allocation-free scratch array
     // one sub-lattice of a lattice split along t (wd_create_split): ranks own consecutive

@@ -104,6 +104,8 @@ cudaError_t launch_apply(const DslashArgs &a, Prec p, int recon, bool dagger, Ds
 cudaError_t launch_apply_staged(const DslashArgs &a, Prec p, int recon, bool dagger, int rows, int stages,
                                 unsigned *err, cudaStream_t st);
 bool staged_ok(Prec p, const Geom &g, int rows, int stages);
+// allocates (and zeroes) the staged kernel's error word of the context on first use
+wd_status staged_error_word(wd_ctx *c);
 // The plain FP32 operator with each thread prefetching its next hops' neighbour spinors into
 // shared memory by cp.async (tiles as for launch_apply, one right-hand side per thread).
 cudaError_t launch_apply_prefetch(const DslashArgs &a, int recon, bool dagger, DslashTiles t, cudaStream_t st);

@@ -506,7 +506,8 @@ struct Scalars {
     int status;
     int reliable;      // number of reliable updates
     int do_update;     // reliable update requested for this iteration
-    int pad[2];
+    int pending;       // batched solver: a deferred reliable update is due (the CG step went on)
+    int pending_since; // and the iteration at which it fell due
 };
 
 __device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
