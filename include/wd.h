@@ -406,8 +406,9 @@ wd_status wd_get_tiles(wd_ctx *ctx, wd_prec prec, int nrhs, int *site_tile, int 
 /* Plain FP32 operators: each thread applies its site's links to k (1 to 4) of its block's
  * right-hand sides, loading each link once for all k (k dividing rhs_tile, and
  * site_tile * rhs_tile / k threads a multiple of 32); wd_autotune considers k = 2, 3, 4
- * beside 1.  Other precisions and the solvers' fused kernels: k = 1 only.  No counterpart in
- * the paper, which has one right-hand side. */
+ * beside 1.  Other precisions, the solvers' fused kernels and split sub-lattices
+ * (WD_ERR_STATE for k > 1): k = 1 only.  No counterpart in the paper, which has one
+ * right-hand side. */
 wd_status wd_set_rhs_per_thread(wd_ctx *ctx, wd_prec prec, int nrhs, int k);
 
 /* Launch-configuration query: number of kernel launches the last wd_* call queued

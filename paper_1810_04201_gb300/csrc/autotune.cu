@@ -6,7 +6,8 @@
 // rhs_tile in {1, 2, 3, 4, 6, 8, 12, 16} right-hand sides per block, with
 // site_tile * rhs_tile <= 256, a multiple of 32, and rhs_tile <= nrhs (FP64 and
 // DF32, two lanes per site: site_tile >= 32, i.e. site_tile / 2 sites per block); for
-// FP32 also 2, 3 or 4 right-hand sides per thread (K dividing rhs_tile).  Each candidate
+// FP32 also 2, 3 or 4 right-hand sides per thread (K dividing rhs_tile; not on a split
+// sub-lattice, whose interior hops need the split_t form of the kernel).  Each candidate
 // runs the plain D kernel twice untimed and five times timed, each timed launch with L2
 // flushed before it (CUDA events on the context stream), on a non-zero input; the fastest
 // is kept for (precision, nrhs) and used by every later operator call, and by the solvers
@@ -82,7 +83,7 @@ wd_status wd_autotune(wd_ctx *c, wd_prec prec, int nrhs, int *site_tile, int *rh
             for (int kt : kts) {
                 if (rt > nrhs || st * rt > 256 || (st * rt) % 32 != 0) continue;
                 if (threads_per_site((Prec)prec) > 1 && st % 32 != 0) continue;
-                if (kt > 1 && (prec != WD_F32 || rt % kt != 0 || (st * rt / kt) % 32 != 0)) continue;
+                if (kt > 1 && (prec != WD_F32 || rt % kt != 0 || (st * rt / kt) % 32 != 0 || c->g.split_t)) continue;
                 DslashTiles t;
                 t.site_tile = st;
                 t.rhs_tile = rt;
@@ -131,6 +132,8 @@ wd_status wd_set_rhs_per_thread(wd_ctx *c, wd_prec prec, int nrhs, int k) {
     DslashTiles t = tiles_for(c, (Prec)prec, nrhs);
     if (k > 1 && (prec != WD_F32 || t.rhs_tile % k != 0 || (t.site_tile * t.rhs_tile / k) % 32 != 0))
         return fail(c, WD_ERR_ARG, "wd_set_rhs_per_thread: FP32 only, k dividing rhs_tile, a multiple of 32 threads");
+    if (k > 1 && c->split)
+        return fail(c, WD_ERR_STATE, "wd_set_rhs_per_thread: a split sub-lattice runs one right-hand side per thread");
     t.rhs_per_thread = k;
     c->tiles[(int)prec * 64 + nrhs] = t;
     return WD_OK;

@@ -9,7 +9,8 @@ template <int P, int RECON, bool DAG>
 static cudaError_t go(const DslashArgs &a, DslashTiles t, cudaStream_t st) {
     if constexpr (P == F32) {
         const int k = t.rhs_per_thread;
-        if (k > 1 && t.rhs_tile % k == 0) {
+        // the K-per-thread kernel has no sub-lattice (split_t) form
+        if (k > 1 && t.rhs_tile % k == 0 && !a.g.split_t) {
             dim3 block(t.site_tile, t.rhs_tile / k);
             dim3 grid(site_blocks<P>(a.g.V, t.site_tile), (a.nrhs + t.rhs_tile - 1) / t.rhs_tile);
             if (k == 2) dslash_multi_kernel<RECON, DAG, 2><<<grid, block, 0, st>>>(a);

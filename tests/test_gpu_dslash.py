@@ -278,7 +278,7 @@ def test_rhs_per_thread_matches_oracle(wd, nrhs, site_tile, rhs_tile, k):
     dims = (6, 4, 4, 6)
     U = gen.haar_links(dims, seed=95)
     psi = gen.gaussian_source(dims, seed=96, nrhs=nrhs)
-    for recon in (18, 12):
+    for recon in (18, 12, 8):
         lat = wd.Lattice(dims)
         lat.set_gauge(U, recon=recon)
         f = lat.pack(psi, 1)

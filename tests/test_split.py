@@ -141,18 +141,19 @@ def split_blocks(wd, dims, nranks, U, antiperiodic=True, recon=18):
     return blocks
 
 
-def split_apply(blocks, kappa, fields, prec, dagger):
+def split_apply(blocks, kappa, fields, prec, dagger, nrhs=1):
     """D (or D^dag) on every block: faces packed, exchanged by device copies, interior and faces."""
     n = len(blocks)
-    to_prev = [b.new_face(prec) for b in blocks]
-    to_next = [b.new_face(prec) for b in blocks]
+    to_prev = [b.new_face(prec, nrhs) for b in blocks]
+    to_next = [b.new_face(prec, nrhs) for b in blocks]
     for b, f, tp, tn in zip(blocks, fields, to_prev, to_next):
-        b.face_pack(f, tp, tn, prec, dagger=dagger)
+        b.face_pack(f, tp, tn, prec, nrhs=nrhs, dagger=dagger)
     outs = []
     for k, (b, f) in enumerate(zip(blocks, fields)):
-        o = b.new_field(prec)
-        b.apply_interior(kappa, f, o, prec, dagger=dagger)
-        b.apply_faces(kappa, to_next[(k - 1) % n].clone(), to_prev[(k + 1) % n].clone(), o, prec, dagger=dagger)
+        o = b.new_field(prec, nrhs)
+        b.apply_interior(kappa, f, o, prec, nrhs=nrhs, dagger=dagger)
+        b.apply_faces(kappa, to_next[(k - 1) % n].clone(), to_prev[(k + 1) % n].clone(), o, prec, nrhs=nrhs,
+                      dagger=dagger)
         outs.append(o)
     return outs
 
@@ -174,6 +175,32 @@ def test_split_operator_matches_unsplit_oracle(wd, dims, nranks, prec, dagger):
     got = np.concatenate([b.unpack(o, prec) for b, o in zip(blocks, outs)])
     want = oracle.apply_D(U, psi, kappa, dims, antiperiodic_t=True, dagger=dagger)
     assert oracle.rel_err(got, want) < TOL[prec]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1])
+def test_split_operator_multi_rhs(wd, prec):
+    """Several right-hand sides per launch on sub-lattices, with the launch shape the autotuner
+    picks; the FP32 kernel with several right-hand sides per thread (which has no sub-lattice
+    form) is neither tuned nor accepted there."""
+    dims, nranks, kappa, nrhs = (4, 6, 4, 8), 2, 0.124, 4
+    U = gen.haar_links(dims, seed=81)
+    psis = np.stack([gen.gaussian_source(dims, seed=82 + j) for j in range(nrhs)])
+    blocks = split_blocks(wd, dims, nranks, U)
+    for b in blocks:
+        b.autotune(prec, nrhs)
+        assert b.tiles(prec, nrhs)[2] == 1
+    if prec == 1:
+        with pytest.raises(wd.WDError):
+            blocks[0].set_rhs_per_thread(prec, nrhs, 2)
+    fields = [b.pack(np.stack([b.split.local_field(p, r) for p in psis]), prec) for r, b in enumerate(blocks)]
+    for dagger in (False, True):
+        outs = split_apply(blocks, kappa, fields, prec, dagger, nrhs)
+        torch.cuda.synchronize()
+        got = np.concatenate([b.unpack(o, prec, nrhs, squeeze=False) for b, o in zip(blocks, outs)], axis=1)
+        for j in range(nrhs):
+            want = oracle.apply_D(U, psis[j], kappa, dims, antiperiodic_t=True, dagger=dagger)
+            assert oracle.rel_err(got[j], want) < TOL[prec], (j, dagger)
 
 
 @pytest.mark.gpu
