@@ -191,8 +191,8 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *              r = D^dag(b - D x) and the solution accumulated in FP64
  *   delta      reliable-update trigger: an update runs when the iterated residual
  *              drops below delta times its maximum since the last update (0 = the
- *              default of the inner precision: 1e-2 for WD_F16, 1e-4 for WD_F32,
- *              1e-6 for WD_DF32)
+ *              default of the inner precision: 1e-2 for WD_F16 (3e-3 with
+ *              precondition = 1), 3e-6 for WD_F32, 1e-6 for WD_DF32)
  *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
  *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
  *              1: block CG (one Krylov space for all right-hand sides, FP64 only)

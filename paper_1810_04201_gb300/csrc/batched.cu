@@ -633,7 +633,7 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     if ((s = ws_get(c0, "bt_tl", sizeof(int) * ntiles, &d_tl)) != WD_OK) return s;
     if ((s = ws_get(c0, "bt_bar", 256, &d_bar)) != WD_OK) return s;
     std::vector<Scalars> h(n);
-    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec);
+    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec, false);
     for (int i = 0; i < n; ++i) {
         std::memset(&h[i], 0, sizeof(Scalars));
         h[i].tol2 = prm->tol * prm->tol;

@@ -197,7 +197,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     // tighter reduced tolerance, until the recomputed full-lattice residual meets tol.
     // With the system-residual rule the same resumption runs until |b - D x| meets tol.
     std::vector<Scalars> h(nrhs);
-    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec);
+    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec, eo);
     void *bin = eo ? f.eo.bfull : f.b, *xin = eo ? f.eo.xfull : f.x;
     WD_CUDA(c, cudaMemcpyAsync(bin, b, sfull, cudaMemcpyDeviceToDevice, c->stream));
     if (pl.ne) WD_CUDA(c, cudaMemsetAsync(xin, 0, sfull, c->stream));  // CGNE starts from y = 0

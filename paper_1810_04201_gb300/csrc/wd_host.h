@@ -12,6 +12,24 @@ namespace wd {
 struct DslashArgs;
 struct VecArgs;
 
+// Default reliable-update threshold per inner precision: an FP64 update runs when
+// the iterated residual has dropped by this factor since the last one.  Low
+// precisions need frequent updates; FP64 updates are expensive on a part with a
+// thin FP64 pipe, so the threshold is as small as each precision allows.  The
+// partial solution of a segment is summed in FP32 for every inner precision, which
+// bounds DF32 too (1e-9 no longer converges).  FP32: 3e-6 takes a 1e-10 solve in
+// two updates (1e-4 took three) at the same iteration count on the 32^3 x 64 and
+// 24^3 x 48 workloads.  FP16: 3e-3 saves two of six updates on the better
+// conditioned even-odd system, but costs 10 % more iterations on the full one.
+inline double default_delta(Prec p, bool eo) {
+    switch (p) {
+    case F16: return eo ? 3e-3 : 1e-2;
+    case F32: return 3e-6;
+    case DF32: return 1e-6;
+    default: return 0.1;
+    }
+}
+
 // status helpers
 wd_status fail(wd_ctx *c, wd_status s, const std::string &msg);
 wd_status cuda_fail(wd_ctx *c, cudaError_t e, const char *where);

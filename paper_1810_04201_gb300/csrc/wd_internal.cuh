@@ -515,19 +515,6 @@ __device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
     return mask == 1 ? sc[r].active != 0 : sc[r].do_update != 0;
 }
 
-// Default reliable-update threshold per inner precision: an FP64 update runs when
-// the iterated residual has dropped by this factor since the last one.  Low
-// precisions need frequent updates; FP64 updates are expensive on a part with a
-// thin FP64 pipe, so the threshold is as small as each precision allows.
-inline double default_delta(Prec p) {
-    switch (p) {
-    case F16: return 1e-2;
-    case F32: return 1e-4;
-    case DF32: return 1e-6;
-    default: return 0.1;
-    }
-}
-
 // Launch shape of a Dslash: blocks of site_tile x rhs_tile (site, right-hand side) pairs; with
 // rhs_per_thread = K > 1 (plain FP32 operator) each thread takes K of the block's right-hand
 // sides, so the block has site_tile x rhs_tile / K threads and loads each link once for K.
