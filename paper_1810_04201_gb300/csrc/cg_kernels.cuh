@@ -19,6 +19,20 @@
 
 namespace wd {
 
+// |v|^2 of one site (or the lane's half site) of an FP32 or FP16-storage field of the
+// inner iteration: the at most 24 squares are summed in FP32 (relative error below
+// 24 u = 1.4e-6, far below what an FP32 recursion resolves) and only the site's total
+// goes on in FP64.  Squaring in FP64 takes 24 FP64 multiply-adds per site and
+// right-hand side on a part with 2 FP64 FMA per SM and clock: 40 us of FP64 pipe per
+// half-lattice pass at 32^3 x 64, and 0.3 ms per pass with 12 right-hand sides at
+// 24^3 x 48.  FP64 and DF32 fields keep the generic FP64 sum.
+template <int N> __device__ __forceinline__ double norm2_of(const C<float> (&v)[N]) {
+    float n = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) n = fmaf(v[c].re, v[c].re, fmaf(v[c].im, v[c].im, n));
+    return (double)n;
+}
+
 // Block + grid reduction of NV doubles per row; `fin(row, tot)` runs once per
 // enabled row, in thread (0, 0) of the last block, rows in order.
 template <int NV, class F>
