@@ -183,8 +183,11 @@ __device__ __forceinline__ void hop64_half(const LatDesc &L, const void *in, int
     for (int k = 0; k < 6; ++k) own[k] = acc[k];
 }
 
+// Five blocks of 128 threads per SM (96 registers): the inner FP32 phases, which wait on
+// loads, gain more from the extra warps than the FP64 phases lose to spills (C5: 54.0 ms
+// at four blocks, 52.7 at five).
 template <int SP, int RECON, int RIN>
-__global__ void __launch_bounds__(kTile, 4) k_batched_cg(BatchArgs a) {
+__global__ void __launch_bounds__(kTile, 5) k_batched_cg(BatchArgs a) {
     using RS = typename Real<SP>::T;
     auto all = [](const Scalars &, int) { return 1; };
     auto active = [](const Scalars &c, int) { return c.active; };
