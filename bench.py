@@ -619,7 +619,8 @@ def cg_variants(wd, torch, lat, w, fb, fx_f64, flush, f64_ms, args):
         ms, (res, st) = _median_solve_ms(torch, flush, solve, reps)
         r = res[0]
         out[name] = {"ms": round(ms, 3), "speedup_vs_f64": round(f64_ms / ms, 3), "iters": r["iters"],
-                     "reliable_updates": r["reliable_updates"], "status": st,
+                     "reliable_updates": r["reliable_updates"], "inner_corrections": r["inner_corrections"],
+                     "status": st,
                      "true_rel_resid": r["true_rel_resid"], "true_rel_resid_b": r["true_rel_resid_b"],
                      "rel_diff_vs_f64_solution": rel_diff(lat.unpack(fx), x64)}
         if rin:
@@ -786,9 +787,11 @@ def compare(args):
             x = lat.unpack(fx)
             sols[name] = x
             line["compare"][name] = {"ms": round(ms, 3), "iters": r["iters"], "reliable_updates": r["reliable_updates"],
+                                     "inner_corrections": r["inner_corrections"],
                                      "status": st, "true_rel_resid_normal": r["true_rel_resid"],
                                      "true_rel_resid_b": r["true_rel_resid_b"],
-                                     "gflops": round((2 * r["iters"] + 4 + 2 * r["reliable_updates"]) * 1320 * V
+                                     "gflops": round((2 * r["iters"] + 4 + 2 * r["reliable_updates"]
+                                                      + 2 * r["inner_corrections"]) * 1320 * V
                                                      / ms / 1e6, 1)}
         for name in variants:
             if name == "f64":

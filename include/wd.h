@@ -252,6 +252,7 @@ typedef struct wd_cg_result {
     double true_rel_resid_b; /* ||b - D x|| / ||b|| of the returned x, in FP64 */
     double seconds;          /* device time of the solve */
     int status;              /* wd_status of this right-hand side */
+    int inner_corrections;   /* FP32 corrections of an FP16 inner iteration (wd_cg_solve) */
 } wd_cg_result;
 
 /* Solve D x = b for nrhs right-hand sides by CG on D^dag D x = D^dag b, entirely on

@@ -706,6 +706,7 @@ extern "C" wd_status wd_cg_solve_batched(wd_ctx *const *ctxs, const double *kapp
     for (int i = 0; i < n; ++i) {
         res[i].iters = h[i].iter;
         res[i].reliable_updates = h[i].reliable;
+        res[i].inner_corrections = 0;
         res[i].true_rel_resid = h[i].rhs2 > 0 ? std::sqrt(h[i].true_n2 / h[i].rhs2) : std::sqrt(h[i].true_n2);
         res[i].true_rel_resid_b = h[i].b2 > 0 ? std::sqrt(h[i].true_b2 / h[i].b2) : std::sqrt(h[i].true_b2);
         res[i].seconds = ms * 1e-3;

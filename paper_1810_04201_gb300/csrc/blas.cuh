@@ -81,7 +81,7 @@ template <int P> __global__ void k_xpby(VecArgs v) {
         if (body > cap + 2) any = 0;  // hard stop: the loop never outlives max_iter
         cudaGraphSetConditional((cudaGraphConditionalHandle)v.cond, any ? 1u : 0u);
     }
-    if (v.sc && blockIdx.x == 0 && threadIdx.x == 0 && r < v.nrhs) v.sc[r].do_update = 0;
+    if (v.sc && blockIdx.x == 0 && threadIdx.x == 0 && r < v.nrhs) v.sc[r].do_update = v.sc[r].do_correct = 0;
     if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
     const R beta = R(v.sc[r].beta);
     C<R> x[12], y[12];
@@ -114,8 +114,8 @@ template <int DUMMY = 0> __global__ void k_reliable_x(VecArgs v) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (v.state && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         int any = 0;
-        for (int k = 0; k < v.nrhs; ++k) any |= v.sc[k].do_update;
-        if (any) v.state[1] += 1;
+        for (int k = 0; k < v.nrhs; ++k) any |= v.sc[k].do_update | v.sc[k].do_correct;
+        if (any) v.state[1] += 1;  // runs of the update branch (a reliable update or a correction)
     }
     if (s >= v.V || !row_on(v.sc, v.mask, r)) return;
     C<double> x[12];

@@ -417,6 +417,7 @@ wd_status block_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const 
     for (int r = 0; r < k; ++r) {
         res[r].iters = hb.iter;
         res[r].reliable_updates = 0;
+        res[r].inner_corrections = 0;
         res[r].true_rel_resid = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
         res[r].true_rel_resid_b = h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2);
         res[r].seconds = ms * 1e-3;

@@ -119,6 +119,14 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         if ((s = ws_get(c, pre + "ts" + sfx, sin, &f.ts)) != WD_OK) return s;
         if ((s = ws_get(c, pre + "xs", spinor_bytes(F32, gw.Vs) * nrhs, &f.xs)) != WD_OK) return s;
     }
+    // An FP16 iteration is corrected in FP32 between its FP64 reliable updates, with an
+    // FP32 copy of the links compressed as the FP64 copy (with another FP32 compression
+    // set on the context, no corrections: the FP64 updates alone, at the FP16 threshold)
+    const bool corr = inner == F16 && link_recon(c, F32) == link_recon(c, F64);
+    if (corr) {
+        if ((s = gauge_get(c, F32, &f.g32)) != WD_OK) return s;
+        if ((s = ws_get(c, pre + "t32c", spinor_bytes(F32, gw.Vs) * nrhs, &f.t32)) != WD_OK) return s;
+    }
     if (eo) {
         f.eo.ge = eo_geom(c, 0);
         f.eo.go = eo_geom(c, 1);
@@ -129,6 +137,12 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
             (s = ws_get(c, std::string("eo_tmps") + std::to_string((int)inner), spinor_bytes(inner, gw.Vs) * nrhs,
                         &f.eo.tmps)) != WD_OK)
             return s;
+        if (corr) {
+            if ((s = gauge_get_eo(c, F32, &f.eo.gauge[F32], &f.eo.gdir[F32])) != WD_OK) return s;
+            if ((s = ws_get(c, std::string("eo_tmps") + std::to_string((int)F32), spinor_bytes(F32, gw.Vs) * nrhs,
+                            &f.eo.tmp32)) != WD_OK)
+                return s;
+        }
         const char *nh[3] = {"eo_be", "eo_bo", "eo_xo"};
         void **ph[3] = {&f.eo.be, &f.eo.bo, &f.eo.xo};
         for (int i = 0; i < 3; ++i)
@@ -168,8 +182,8 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         }
     }
     char key[256];
-    snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d", (int)inner, nrhs, r64, rin, kappa, pl.t64.site_tile,
-             pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo);
+    snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d|%d", (int)inner, nrhs, r64, rin, kappa,
+             pl.t64.site_tile, pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo, corr ? 1 : 0);
     const char *loop_env = getenv("WD_CG_LOOP");
     const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
     cudaGraphExec_t exec = nullptr;
@@ -197,13 +211,13 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     // tighter reduced tolerance, until the recomputed full-lattice residual meets tol.
     // With the system-residual rule the same resumption runs until |b - D x| meets tol.
     std::vector<Scalars> h(nrhs);
-    const double delta = prm->delta > 0 ? prm->delta : default_delta((Prec)prm->inner_prec, eo);
+    const double delta = prm->delta > 0 ? prm->delta : corr ? default_delta(F32, eo) : default_delta(inner, eo);
     void *bin = eo ? f.eo.bfull : f.b, *xin = eo ? f.eo.xfull : f.x;
     WD_CUDA(c, cudaMemcpyAsync(bin, b, sfull, cudaMemcpyDeviceToDevice, c->stream));
     if (pl.ne) WD_CUDA(c, cudaMemsetAsync(xin, 0, sfull, c->stream));  // CGNE starts from y = 0
     else WD_CUDA(c, cudaMemcpyAsync(xin, x, sfull, cudaMemcpyDeviceToDevice, c->stream));
     double tol_run = eo ? 0.5 * prm->tol : prm->tol;
-    std::vector<int> iters(nrhs, 0), reliable(nrhs, 0);
+    std::vector<int> iters(nrhs, 0), reliable(nrhs, 0), corrections(nrhs, 0);
     float ms_total = 0.f;
     long long launches = 0;
     const int attempts = (eo || stop_sys) ? 4 : 1;
@@ -213,6 +227,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
             h[r].tol2 = tol_run * tol_run;
             h[r].max_iter = prm->max_iter - iters[r] > 0 ? prm->max_iter - iters[r] : 0;
             h[r].delta2 = delta * delta;
+            h[r].delta2_lo = corr ? kCorrectDelta * kCorrectDelta : 0.0;
             h[r].active = 1;
             h[r].status = WD_ERR_NOT_CONVERGED;
         }
@@ -247,6 +262,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         for (int r = 0; r < nrhs; ++r) {
             iters[r] += h[r].iter;
             reliable[r] += h[r].reliable;
+            corrections[r] += h[r].corrections;
             all_ok &= h[r].status == WD_OK;
             const double tr = stop_sys ? (h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2))
                                        : (h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2));
@@ -265,6 +281,7 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     for (int r = 0; r < nrhs; ++r) {
         res[r].iters = iters[r];
         res[r].reliable_updates = reliable[r];
+        res[r].inner_corrections = corrections[r];
         res[r].true_rel_resid = h[r].rhs2 > 0 ? std::sqrt(h[r].true_n2 / h[r].rhs2) : std::sqrt(h[r].true_n2);
         res[r].true_rel_resid_b = h[r].b2 > 0 ? std::sqrt(h[r].true_b2 / h[r].b2) : std::sqrt(h[r].true_b2);
         res[r].seconds = ms_total * 1e-3;

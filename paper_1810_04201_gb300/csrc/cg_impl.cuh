@@ -150,6 +150,20 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
                 add_op<F64, RECON, OP2, EpReliable, EO>(ib, r, pl.t64, true, f);
                 v.a = f.r; v.a_stride = s64; v.b = f.rs; v.b_stride = sin;
                 add_vec(ib, k_convert<F64, SP>, v);
+                if constexpr (SP == F16) {
+                    if (f.t32) {
+                        // FP32 correction (rows with do_correct): t32 = A1 xs; rs = r64 - A2 t32
+                        DslashArgs q = base;
+                        q.mask = 3;
+                        q.gauge = f.g32;
+                        q.gauge_dir = gauge_dir_bytes(c, F32);
+                        q.in_stride = q.out_stride = s32;
+                        q.in = f.xs; q.out = f.t32;
+                        add_op<F32, RECON, OP1, EpXpay, EO>(ib, q, pl.tin, false, f);
+                        q.in = f.t32; q.a0 = f.r; q.a0_stride = s64; q.a1 = f.rs; q.a1_stride = sin;
+                        add_op<F32, RECON, OP2, EpCorrect<SP>, EO>(ib, q, pl.tin, true, f);
+                    }
+                }
             }
             bb.cur = &plan.post;
             VecArgs v = vb;

@@ -115,6 +115,7 @@ struct EpSetupR {
             Scalars &c = a.sc[row];
             c.rho = t[0];
             c.rmax2 = t[0];
+            c.rmax2_lo = t[0];
             c.iter = 0;
             if (!is_fin(t[0])) { c.status = WD_ERR_NONFINITE; c.active = 0; }
             else if (t[0] <= c.tol2) { c.status = WD_OK; c.active = 0; }
@@ -227,10 +228,14 @@ struct EpCG2Mixed {
             if (rn <= c.tol2 || rn < c.delta2 * c.rmax2 || c.iter >= c.max_iter) {
                 c.do_update = 1;
                 any = 1;
+            } else if (rn < c.delta2_lo * c.rmax2_lo) {
+                c.do_correct = 1;  // beta and rho follow from the corrected residual
+                any = 1;
             } else {
                 c.beta = rn / c.rho;
                 c.rho = rn;
                 c.rmax2 = fmax(c.rmax2, rn);
+                c.rmax2_lo = fmax(c.rmax2_lo, rn);
             }
         });
         // the if-condition keeps its value across loop iterations: set it every time
@@ -264,6 +269,7 @@ struct EpReliable {
             c.beta = rt / c.rho;
             c.rho = rt;
             c.rmax2 = rt;
+            c.rmax2_lo = rt;
             if (rt <= c.tol2) { c.status = WD_OK; c.active = 0; }
             else if (c.iter >= c.max_iter) { c.status = WD_ERR_NOT_CONVERGED; c.active = 0; }
             if (!c.active && a.state) {
@@ -274,6 +280,45 @@ struct EpReliable {
                 a.state[3] += 1;
                 a.state[4] = a.state[3] < a.nrhs;
             }
+        });
+    }
+};
+
+// FP32 correction of an FP16 inner iteration (a P = FP32 kernel): with x = x64 + xs and
+// r64 = b' - A x64 the FP64 residual of the last reliable update (a0), the residual of x
+// is r64 - A xs; here q = (A xs) from the second operator pass, r = r64 - q goes to the
+// inner field (a1, FP16 storage) and rho = |r|^2.  Its error, about 2^-24 |r64|, stays
+// below the FP16 recursion's as long as |r| > 2^-24 |r64| / 1e-2, which the FP64
+// threshold delta keeps.  No counterpart in the paper (a three-level reliable update).
+template <int SP>
+struct EpCorrect {
+    struct State { double v[1]; };
+    template <int P, class R, class Pt>
+    static __device__ __forceinline__ void site(const DslashArgs &a, int s, int r, const void *in, C<R> (&acc)[Pt::N],
+                                                State &st, const Pt &pt) {
+        static_assert(P == F32, "the correction runs in FP32");
+        C<R> q[Pt::N];
+        load_part<P>(pt, in, a.g.Vs, s, q);
+        xpay_site(q, acc, R(a.kappa));
+        C<double> b[Pt::N];
+        load_part<F64>(pt, rhs_ptr<double>(a.a0, a.a0_stride, r), a.g.Vs, s, b);
+        C<float> d[Pt::N];
+#pragma unroll
+        for (int c = 0; c < Pt::N; ++c) d[c] = C<float>{float(b[c].re) - q[c].re, float(b[c].im) - q[c].im};
+        st.v[0] += norm2_of(d);
+        store_part<SP>(pt, rhs_ptr<float>(a.a1, a.a1_stride, r), a.g.Vs, s, d);
+    }
+    template <int P>
+    static __device__ __forceinline__ void finish(const DslashArgs &a, int, bool, State &st) {
+        reduce_finish<1>(a, st.v, [&](int row, const double *t) {
+            Scalars &c = a.sc[row];
+            const double rt = t[0];
+            c.corrections += 1;
+            if (!is_fin(rt)) { c.status = WD_ERR_NONFINITE; c.active = 0; return; }
+            c.beta = rt / c.rho;
+            c.rho = rt;
+            c.rmax2 = fmax(c.rmax2, rt);
+            c.rmax2_lo = rt;
         });
     }
 };

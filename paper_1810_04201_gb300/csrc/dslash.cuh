@@ -35,7 +35,7 @@ struct DslashArgs {
     void *a2; size_t a2_stride;
     const void *a3; size_t a3_stride;
     Scalars *sc;               // per right-hand-side solver state (nullptr: plain operator)
-    int mask;                  // rows to process: 0 all, 1 active, 2 reliable update pending
+    int mask;                  // rows to process: 0 all, 1 active, 2 reliable update, 3 FP32 correction
     double *partial;           // per-block partial sums
     unsigned *counter;         // last-block ticket
     unsigned long long cond;   // cudaGraphConditionalHandle to set (0 = none)

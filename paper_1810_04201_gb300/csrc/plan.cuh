@@ -111,6 +111,7 @@ struct EoInfo {
     const void *gauge[kNumPrec];          // checkerboard gauge per precision
     size_t gdir[kNumPrec];
     void *tmp64, *tmps;                   // odd-parity temporaries (FP64, inner precision)
+    void *tmp32;                          // and FP32, for the corrections of an FP16 iteration
     void *bfull, *xfull, *tfull, *dbfull; // full-lattice fields for the split, join and final check
     void *be, *bo, *xo;                   // even / odd halves
 };
@@ -118,6 +119,8 @@ struct EoInfo {
 struct Fields {
     void *b, *x, *db, *r, *p, *t;      // FP64
     void *rs, *ps, *ts, *xs;            // inner precision (xs FP32)
+    void *t32;                          // FP16 iteration: FP32 field of the corrections (null: none)
+    const void *g32;                    // and the FP32 links they use
     Scalars *sc;
     double *partial;
     unsigned *counter;
@@ -160,7 +163,7 @@ static void add_op(GraphBuilder &gb, const DslashArgs &a, DslashTiles t, bool re
         add_dslash<P, RECON, DAG, Ep>(gb, a, t, reduce);
     } else {
         const size_t sp = spinor_bytes((Prec)P, f.eo.ge.Vs);
-        void *tmp = P == F64 ? f.eo.tmp64 : f.eo.tmps;
+        void *tmp = P == F64 ? f.eo.tmp64 : (P == F32 && f.eo.tmp32) ? f.eo.tmp32 : f.eo.tmps;
         DslashArgs h = a;
         h.g = f.eo.go;
         h.gauge = f.eo.gauge[P];

@@ -586,6 +586,7 @@ extern "C" wd_status wd_cg_solve_split(wd_ctx *const *ctxs, int n, double kappa,
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     res->iters = k;
     res->reliable_updates = 0;
+    res->inner_corrections = 0;
     res->true_rel_resid = ndb2 > 0 ? std::sqrt(nde2 / ndb2) : std::sqrt(nde2);
     res->true_rel_resid_b = nb2 > 0 ? std::sqrt(ne2 / nb2) : std::sqrt(ne2);
     res->seconds = secs;

@@ -21,6 +21,11 @@ struct VecArgs;
 // two updates (1e-4 took three) at the same iteration count on the 32^3 x 64 and
 // 24^3 x 48 workloads.  FP16: 3e-3 saves two of six updates on the better
 // conditioned even-odd system, but costs 10 % more iterations on the full one.
+// FP32 corrections of an FP16 inner iteration run when its residual has dropped by
+// this factor since the last correction or reliable update (FP16 storage resolves about
+// three decimal digits; the FP64 updates then follow the FP32 threshold).
+constexpr double kCorrectDelta = 1e-2;
+
 inline double default_delta(Prec p, bool eo) {
     switch (p) {
     case F16: return eo ? 3e-3 : 1e-2;

@@ -508,11 +508,15 @@ struct Scalars {
     int do_update;     // reliable update requested for this iteration
     int pending;       // batched solver: a deferred reliable update is due (the CG step went on)
     int pending_since; // and the iteration at which it fell due
+    double delta2_lo;  // FP16 inner iteration: FP32 correction threshold (0: none)
+    double rmax2_lo;   // max |r|^2 since the last correction or reliable update
+    int do_correct;    // FP32 correction requested for this iteration
+    int corrections;   // FP32 corrections run
 };
 
 __device__ __forceinline__ bool row_on(const Scalars *sc, int mask, int r) {
     if (mask == 0 || sc == nullptr) return true;
-    return mask == 1 ? sc[r].active != 0 : sc[r].do_update != 0;
+    return mask == 1 ? sc[r].active != 0 : mask == 3 ? sc[r].do_correct != 0 : sc[r].do_update != 0;
 }
 
 // Launch shape of a Dslash: blocks of site_tile x rhs_tile (site, right-hand side) pairs; with

@@ -34,7 +34,8 @@ class CGParams(ctypes.Structure):
 
 class CGResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
-                ("true_rel_resid_b", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("true_rel_resid_b", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("inner_corrections", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
