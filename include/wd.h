@@ -188,11 +188,16 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *   inner_prec WD_F64: plain FP64 CG.  WD_F32 / WD_F16 / WD_DF32: mixed precision --
  *              the Dslash and the inner iteration in FP32 (or FP16 storage with FP32
  *              accumulation, or double-FP32), with FP64 reliable updates
- *              r = D^dag(b - D x) and the solution accumulated in FP64
+ *              r = D^dag(b - D x) and the solution accumulated in FP64.  WD_F16 (when
+ *              the FP32 link copy has the FP64 copy's compression): between the FP64
+ *              updates, each time the residual has dropped by 1e-2, the residual is
+ *              corrected in FP32 from the last FP64 one, r = r64 - A xs (xs the FP32
+ *              partial solution since that update; wd_cg_result.inner_corrections)
  *   delta      reliable-update trigger: an update runs when the iterated residual
  *              drops below delta times its maximum since the last update (0 = the
- *              default of the inner precision: 1e-2 for WD_F16 (3e-3 with
- *              precondition = 1), 3e-6 for WD_F32, 1e-6 for WD_DF32)
+ *              default of the inner precision: 3e-6 for WD_F32 and for WD_F16 with
+ *              FP32 corrections, 1e-2 for WD_F16 without (3e-3 with precondition =
+ *              1), 1e-6 for WD_DF32)
  *   nrhs       number of right-hand sides in b and x (1..WD_MAX_RHS)
  *   block      0: nrhs independent CG recursions sharing each multi-RHS Dslash;
  *              1: block CG (one Krylov space for all right-hand sides, FP64 only)
