@@ -119,10 +119,13 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
         if ((s = ws_get(c, pre + "ts" + sfx, sin, &f.ts)) != WD_OK) return s;
         if ((s = ws_get(c, pre + "xs", spinor_bytes(F32, gw.Vs) * nrhs, &f.xs)) != WD_OK) return s;
     }
-    // An FP16 iteration is corrected in FP32 between its FP64 reliable updates, with an
-    // FP32 copy of the links compressed as the FP64 copy (with another FP32 compression
-    // set on the context, no corrections: the FP64 updates alone, at the FP16 threshold)
-    const bool corr = inner == F16 && link_recon(c, F32) == link_recon(c, F64);
+    // An FP16 iteration is corrected in FP32 between its FP64 reliable updates, with the
+    // FP32 copy of the links, compressed as the FP64 copy or as the FP16 one (with a third
+    // compression on the FP32 copy, no corrections: the FP64 updates alone, at the FP16
+    // threshold)
+    const int rc32 = link_recon(c, F32);
+    const bool corr = inner == F16 && (rc32 == link_recon(c, F64) || rc32 == link_recon(c, F16));
+    f.c32_inner = corr && rc32 != link_recon(c, F64);
     if (corr) {
         if ((s = gauge_get(c, F32, &f.g32)) != WD_OK) return s;
         if ((s = ws_get(c, pre + "t32c", spinor_bytes(F32, gw.Vs) * nrhs, &f.t32)) != WD_OK) return s;
@@ -183,7 +186,8 @@ wd_status wd_cg_solve(wd_ctx *c, double kappa, const void *b, void *x, const wd_
     }
     char key[256];
     snprintf(key, sizeof key, "cg|%d|%d|%d,%d|%a|%d,%d|%d,%d|%d|%d|%d", (int)inner, nrhs, r64, rin, kappa,
-             pl.t64.site_tile, pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo, corr ? 1 : 0);
+             pl.t64.site_tile, pl.t64.rhs_tile, pl.tin.site_tile, pl.tin.rhs_tile, pl.ne, pl.eo,
+             corr ? 1 + f.c32_inner : 0);
     const char *loop_env = getenv("WD_CG_LOOP");
     const bool host_loop = loop_env && std::strcmp(loop_env, "host") == 0;
     cudaGraphExec_t exec = nullptr;

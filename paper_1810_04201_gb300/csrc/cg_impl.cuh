@@ -152,16 +152,23 @@ static void record_plan(wd_ctx *c, const SolverPlan &pl, const Fields &f, const 
                 add_vec(ib, k_convert<F64, SP>, v);
                 if constexpr (SP == F16) {
                     if (f.t32) {
-                        // FP32 correction (rows with do_correct): t32 = A1 xs; rs = r64 - A2 t32
+                        // FP32 correction (rows with do_correct): t32 = A1 xs; rs = r64 - A2 t32,
+                        // on the FP32 links (compressed as the FP64 copy, or as the inner one)
                         DslashArgs q = base;
                         q.mask = 3;
                         q.gauge = f.g32;
                         q.gauge_dir = gauge_dir_bytes(c, F32);
                         q.in_stride = q.out_stride = s32;
                         q.in = f.xs; q.out = f.t32;
-                        add_op<F32, RECON, OP1, EpXpay, EO>(ib, q, pl.tin, false, f);
-                        q.in = f.t32; q.a0 = f.r; q.a0_stride = s64; q.a1 = f.rs; q.a1_stride = sin;
-                        add_op<F32, RECON, OP2, EpCorrect<SP>, EO>(ib, q, pl.tin, true, f);
+                        DslashArgs q2 = q;
+                        q2.in = f.t32; q2.a0 = f.r; q2.a0_stride = s64; q2.a1 = f.rs; q2.a1_stride = sin;
+                        if (f.c32_inner) {
+                            add_op<F32, RIN, OP1, EpXpay, EO>(ib, q, pl.tin, false, f);
+                            add_op<F32, RIN, OP2, EpCorrect<SP>, EO>(ib, q2, pl.tin, true, f);
+                        } else {
+                            add_op<F32, RECON, OP1, EpXpay, EO>(ib, q, pl.tin, false, f);
+                            add_op<F32, RECON, OP2, EpCorrect<SP>, EO>(ib, q2, pl.tin, true, f);
+                        }
                     }
                 }
             }

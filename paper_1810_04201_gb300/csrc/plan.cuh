@@ -120,7 +120,8 @@ struct Fields {
     void *b, *x, *db, *r, *p, *t;      // FP64
     void *rs, *ps, *ts, *xs;            // inner precision (xs FP32)
     void *t32;                          // FP16 iteration: FP32 field of the corrections (null: none)
-    const void *g32;                    // and the FP32 links they use
+    const void *g32;                    // and the FP32 links they use,
+    int c32_inner;                      // compressed as the inner links (1) or the FP64 ones (0)
     Scalars *sc;
     double *partial;
     unsigned *counter;

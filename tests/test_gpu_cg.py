@@ -401,6 +401,27 @@ def test_whole_fp64_links_with_compressed_inner_links(wd, inner, rin, eo):
     assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
 
 
+@pytest.mark.parametrize("r16,r32,eo", [(12, 12, 0), (12, 12, 1), (8, 8, 0), (12, 18, 1), (12, 8, 0)])
+def test_fp16_iteration_fp32_corrections(wd, r16, r32, eo):
+    """FP16 inner iterations corrected in FP32 between the FP64 reliable updates, on FP32
+    links compressed as the FP64 copy (18) or as the FP16 copy; with a third compression
+    on the FP32 copy there are no corrections.  Every variant reaches the oracle's solution."""
+    dims, kappa = (6, 4, 4, 8), 0.124
+    U = gen.haar_links(dims, seed=45)
+    b = gen.gaussian_source(dims, seed=46)
+    x_ref, _ = ref_solution(U, b, kappa, dims)
+    lat = wd.Lattice(dims)
+    lat.set_gauge(U, recon=18)
+    lat.set_link_compression(2, r16)
+    if r32 != 18:
+        lat.set_link_compression(1, r32)
+    fx = lat.new_field()
+    res, st = lat.cg(kappa, lat.pack(b), fx, tol=1e-10, inner=2, precondition=eo)
+    assert st == 0 and res[0]["true_rel_resid"] <= 1e-10 and res[0]["reliable_updates"] >= 1
+    assert oracle.rel_err(lat.unpack(fx), x_ref) < 1e-9
+    assert (res[0]["inner_corrections"] > 0) == (r32 in (18, r16))
+
+
 def test_link_compression_rules(wd):
     dims, kappa = (4, 4, 4, 4), 0.12
     U = gen.haar_links(dims, seed=43)
