@@ -189,10 +189,11 @@ wd_status wd_apply_schur(wd_ctx *ctx, double kappa, const void *in, void *out, i
  *              the Dslash and the inner iteration in FP32 (or FP16 storage with FP32
  *              accumulation, or double-FP32), with FP64 reliable updates
  *              r = D^dag(b - D x) and the solution accumulated in FP64.  WD_F16 (when
- *              the FP32 link copy is compressed as the FP64 or the FP16 copy): between the FP64
- *              updates, each time the residual has dropped by 1e-2, the residual is
- *              corrected in FP32 from the last FP64 one, r = r64 - A xs (xs the FP32
- *              partial solution since that update; wd_cg_result.inner_corrections)
+ *              the FP32 link copy is compressed as the FP64 or the FP16 copy): between
+ *              the FP64 updates, each time the residual has dropped by 1e-2, the
+ *              residual is corrected in FP32 from the last FP64 one, r = r64 - A xs
+ *              (xs the FP32 partial solution since that update;
+ *              wd_cg_result.inner_corrections)
  *   delta      reliable-update trigger: an update runs when the iterated residual
  *              drops below delta times its maximum since the last update (0 = the
  *              default of the inner precision: 3e-6 for WD_F32 and for WD_F16 with
