@@ -12,7 +12,8 @@
 // precision, the partial solution xs in FP32); when |r|^2 drops below delta^2
 // times its value at the last update (or below the tolerance), a reliable update
 // runs in FP64: x += xs, xs = 0, r = D^dag (b - D x), rho = |r|^2, and r is
-// copied back to the inner precision.
+// copied back to the inner precision.  An FP16 iteration is also corrected in FP32
+// in between (EpCorrect): r = r64 - A xs from the last FP64 residual r64.
 #pragma once
 #include "dslash.cuh"
 #include "blas.cuh"
