@@ -83,3 +83,30 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
                     "-L", os.path.dirname(so), "-lwd", "-Wl,-rpath," + os.path.dirname(so)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert int(out[0]) == len(names)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct of wd.h has the size and field offsets of its ctypes mirror in the
+    binding (a field added on one side only would shift the others)."""
+    import subprocess
+    from paper_1810_04201_gb300 import wd
+    mirrors = {"wd_cg_params": wd.CGParams, "wd_cg_result": wd.CGResult, "wd_comm": wd.Comm}
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "wd.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        prog.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            prog.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    prog += ["    return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[cname, field] = int(value)
+    for cname, py in mirrors.items():
+        assert got[cname, "size"] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[cname, field] == getattr(py, field).offset, (cname, field)
